@@ -1,0 +1,218 @@
+/*
+ * sme.h -- C ABI of the GB300 (sm_103a) library for stochastic matrix-free
+ * equilibration (Diamond & Boyd, "Stochastic Matrix-Free Equilibration").
+ *
+ * The library finds diagonal scalings D = diag(e^u), E = diag(e^v) that
+ * approximately equilibrate A in the l2 norm (Section 1: rows of DAE with norm
+ * alpha, columns with norm beta, m alpha^2 = n beta^2), by projected stochastic
+ * gradient on the regularised, box-constrained problem (eq. (3), Section 2.3)
+ * with the randomised row-norm estimator of Section 3.1 (Algorithm 1), and then
+ * uses D and E as a diagonal preconditioner for LSQR (Section 5.1).
+ *
+ * Conventions shared by every entry point
+ *   - All pointers to vectors are DEVICE pointers unless the argument says
+ *     "host".  Vectors are dense, contiguous, in the op's state type: double
+ *     for an SME_F64 op, float otherwise.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued on it in order; an entry point that returns host results
+ *     synchronises that stream before returning and says so.
+ *   - Errors are returned as sme_status; nothing throws across the ABI.
+ *     sme_last_error() gives a one-line description of the last failure on
+ *     the calling thread.  After SME_ERR_CUDA the op should be destroyed.
+ *   - The op owns its device copies of A and all scratch it allocates; the
+ *     caller owns every vector it passes in.
+ *   - Indices are 0-based.  m, n >= 1; nnz < 2^31.
+ */
+#ifndef SME_H
+#define SME_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sme_op_s *sme_op;
+
+typedef enum {
+    SME_OK = 0,
+    SME_ERR_ARG = -1,           /* a null pointer, a size out of range or an inconsistent parameter */
+    SME_ERR_INVALID_CSR = -2,   /* row_ptr not monotone / not starting at 0 / not ending at nnz, a column
+                                   index outside [0, n), or columns not strictly increasing in a row */
+    SME_ERR_OOM = -3,           /* a device allocation failed */
+    SME_ERR_CUDA = -4,          /* a CUDA runtime call failed */
+    SME_ERR_NONFINITE = -5,     /* a NaN or Inf in the input values or in an iterate */
+    SME_ERR_TIMEOUT = -6,       /* a bounded device-side wait gave up */
+    SME_ERR_NOT_CONVERGED = -7, /* LSQR stopped at max_iters above its tolerance (results still written) */
+    SME_ERR_UNSUPPORTED = -8    /* a valid request this build does not implement (e.g. an unsupported k) */
+} sme_status;
+
+typedef enum {
+    SME_F64 = 0,   /* double values, double state vectors */
+    SME_F32 = 1,   /* float values, float state vectors */
+    SME_BF16 = 2,  /* dense only: bfloat16 values, float state vectors */
+    SME_FP8E4M3 = 3 /* dense only: e4m3 values with one float scale per row, float state vectors */
+} sme_dtype;
+
+const char *sme_status_string(sme_status s);
+const char *sme_last_error(void);
+
+/* ------------------------------------------------------------------ operators */
+
+/*
+ * sme_op_create_csr -- build the operator for a sparse A (m x n) given in CSR.
+ *
+ * The method touches A only through products with A and A^T (Section 3,
+ * "matrix-free").  The op keeps, on the device:
+ *   - a sliced-ELL copy of A (32-row slices, rows ordered by length), for A.x;
+ *   - a transposed copy built ON THE DEVICE from the CSR by a stable radix
+ *     sort on column index (no atomics in the products), for A^T.y.
+ * row_ptr: int32[m+1], row_ptr[0] = 0, non-decreasing, row_ptr[m] = nnz.
+ * col_idx: int32[nnz], strictly increasing within each row, in [0, n).
+ * vals:    nnz values of `dtype` (SME_F64 or SME_F32).
+ * on_device = 0: the three arrays are host memory (validated on the host);
+ * on_device = 1: they are device memory (validated by a device check).
+ * Empty rows and columns are allowed (problem (3) stays bounded, Section 2.3).
+ * Synchronises `stream`.  Returns SME_ERR_INVALID_CSR / SME_ERR_NONFINITE on bad input.
+ */
+sme_status sme_op_create_csr(sme_op *out, int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr,
+                             const int32_t *col_idx, const void *vals, sme_dtype dtype, int on_device,
+                             void *stream);
+
+/*
+ * sme_op_create_dense -- build the operator for a dense row-major A (m x n).
+ * dtype SME_BF16: A is bfloat16, lda >= n elements.
+ * dtype SME_FP8E4M3: A is e4m3 (one byte per entry), row_scales[m] floats with
+ *   A_ij = row_scales[i] * e4m3(A_ij); pass NULL for unit scales.
+ * Products with the +-1 probe blocks run on the tcgen05 tensor cores with FP32
+ * accumulation (Section 3.1 estimator, dense A).  m and n must be multiples of 128.
+ * on_device as for the CSR form.  Synchronises `stream`.
+ */
+sme_status sme_op_create_dense(sme_op *out, int64_t m, int64_t n, const void *A, int64_t lda, sme_dtype dtype,
+                               const float *row_scales, int on_device, void *stream);
+
+sme_status sme_op_destroy(sme_op op);
+
+typedef struct {
+    int64_t m, n, nnz;          /* nnz = m*n for a dense op */
+    int32_t dtype;              /* sme_dtype of the values */
+    int32_t state_is_double;    /* 1 when state vectors are double */
+    int64_t device_bytes;       /* device memory the op holds */
+    int64_t padded_entries_fwd; /* sliced-ELL entries incl. padding, A and A^T copies */
+    int64_t padded_entries_bwd;
+} sme_op_info;
+
+sme_status sme_op_get_info(sme_op op, sme_op_info *info);
+
+/* ------------------------------------------------------------------ probes */
+
+/*
+ * sme_draw_probes -- the IID uniform {-1,+1} probe draw of Algorithm 1, as bits.
+ *
+ * Philox4x32-10 (Salmon et al., SC'11) with
+ *   key = (seed mod 2^32, seed >> 32), counter = (index, t, stream_id, p >> 7),
+ *   word = out[(p >> 5) & 3], sign of probe p at `index` = bit (p & 31) set ? -1 : +1.
+ * Writes words[w * len + index] for w < ceil(k/32), index < len (device uint32).
+ * Stream ids: 2*b for s (columns) and 2*b+1 for w (rows) of matrix b of a batch.
+ */
+sme_status sme_draw_probes(uint64_t seed, int32_t t, int32_t stream_id, int64_t len, int32_t k,
+                           uint32_t *words, void *stream);
+
+/* ------------------------------------------------------------------ equilibration */
+
+typedef struct {
+    double alpha, beta;   /* target row / column norms; <= 0 selects (n/m)^(1/4), (m/n)^(1/4) (Section 4) */
+    double gamma;         /* regularisation of eq. (3); <= 0 selects 0.1 (Section 4) */
+    double M;             /* box |u|,|v| <= M of eq. (3); <= 0 selects log(1e4) (Section 4) */
+    int32_t T;            /* iterations performed by this call, >= 0 */
+    int32_t k;            /* probes per iteration (estimates averaged over the k probes); 1,2,4,...,64 */
+    int32_t t_begin;      /* index t of the first iteration (>= 1); > 1 resumes a run */
+    int32_t t0;           /* step offset: eta_t = 2 / (gamma (t + t0 + 1)); 0 is Algorithm 1 */
+    uint64_t seed;        /* Philox key for the probes */
+    int32_t stream_base;  /* Philox stream pair: stream_base for s, stream_base + 1 for w */
+    int32_t flags;        /* SME_EQ_* bits */
+} sme_equil_params;
+
+#define SME_EQ_ASYNC 1    /* do not synchronise or read the status word; see sme_op_check */
+#define SME_EQ_NO_GRAPH 2 /* launch the iterations directly instead of through a cached CUDA graph */
+
+/*
+ * sme_equilibrate -- iterations t_begin .. t_begin+T-1 of Algorithm 1 (Section 3.2):
+ *   D = diag(e^{u^{t-1}}), E = diag(e^{v^{t-1}});
+ *   z_u = (1/k) sum_p |D A E s_p|^2,  z_v = (1/k) sum_p |E A^T D w_p|^2   (both from the previous iterate);
+ *   u^t = Pi_[-M,M](u^{t-1} - 2 (z_u - alpha^2 + gamma u^{t-1}) / (gamma (t + t0 + 1))), v^t likewise;
+ *   ubar <- 2 u^t / (t + 2) + t ubar / (t + 2), vbar likewise.
+ * u[m], v[n]: in: u^{t_begin-1}, v^{t_begin-1} (zeros for the paper's start); out: the last iterate.
+ * u_bar[m], v_bar[n]: in: the averages after t_begin-1 iterations (zeros at the start); out: updated.
+ * The outputs D = diag(e^{u_bar}), E = diag(e^{v_bar}) are the method's result.
+ * Unless SME_EQ_ASYNC, synchronises `stream` and returns SME_ERR_NONFINITE if an iterate was not finite.
+ */
+sme_status sme_equilibrate(sme_op op, const sme_equil_params *p, void *u, void *v, void *u_bar, void *v_bar,
+                           void *stream);
+
+/* sme_op_check -- synchronise `stream`, return and clear the op's device status word. */
+sme_status sme_op_check(sme_op op, void *stream);
+
+/*
+ * sme_estimate -- the estimator alone (Section 3.1) for iteration t's probes:
+ *   z_u[i] = (1/k) sum_p ((D A E s_p)_i)^2,  z_v[j] = (1/k) sum_p ((E A^T D w_p)_j)^2
+ * with D = diag(e^u), E = diag(e^v), probes from (seed, t, stream_base[+1]).  z_u[m], z_v[n] device
+ * outputs in the state type; either may be NULL to skip it.
+ */
+sme_status sme_estimate(sme_op op, const void *u, const void *v, int32_t t, int32_t k, uint64_t seed,
+                        int32_t stream_base, void *z_u, void *z_v, void *stream);
+
+/* ------------------------------------------------------------------ evaluation */
+
+typedef struct {
+    double row_spread;   /* max/min l2 norm over nonempty rows of DAE */
+    double col_spread;   /* max/min l2 norm over nonempty columns of DAE */
+    double rms;          /* RMS equilibration error (Section 4) */
+    double objective;    /* f(u, v) of eq. (3) */
+    int64_t empty_rows, empty_cols;
+} sme_eval_result;
+
+/*
+ * sme_evaluate -- exact squared row and column norms of DAE (the optimality
+ * conditions of Section 2.1) with FP64 accumulation, and the metrics above.
+ * r2[m], c2[n]: optional device outputs (double), may be NULL.  `res` is a host
+ * struct.  alpha, beta, gamma <= 0 select the Section 4 defaults.  Synchronises `stream`.
+ */
+sme_status sme_evaluate(sme_op op, const void *u, const void *v, double alpha, double beta, double gamma,
+                        double *r2, double *c2, sme_eval_result *res, void *stream);
+
+/* ------------------------------------------------------------------ LSQR */
+
+typedef struct {
+    double tol;          /* stop when the selected residual <= tol (e.g. 1e-6) */
+    int64_t max_iters;   /* iteration cap */
+    int32_t check_every; /* true residual (FP64) checked every this many iterations (>= 1) */
+    int32_t stop_rule;   /* 0: ||A x - b|| / ||b||;  1: ||A^T r|| / (||A||_F ||r||) (least squares) */
+} sme_lsqr_params;
+
+typedef struct {
+    int64_t iters;            /* LSQR iterations performed */
+    double rel_residual;      /* ||A x - b|| / ||b|| of the ORIGINAL system, FP64 */
+    double normal_residual;   /* ||A^T (A x - b)|| / (||A||_F ||A x - b||), FP64 */
+    int32_t converged;
+} sme_lsqr_result;
+
+/*
+ * sme_lsqr -- LSQR (Paige & Saunders 1982) on the equilibrated operator (Section 5.1):
+ * solves (D A E) xbar = D b from xbar = 0 and returns x = E xbar.  D = diag(e^{u_bar}),
+ * E = diag(e^{v_bar}); u_bar == NULL means D = I (column scaling only, which keeps the
+ * least-squares minimiser of an inconsistent system), and both NULL is plain LSQR.
+ * Vectors are in the state type; the scalar recurrences (rho, phibar, norms) and the
+ * residual checks run in FP64 on the device, so there is no host round trip per iteration.
+ * b[m] device input, x[n] device output.  Synchronises `stream`; `res` is a host struct.
+ * Returns SME_ERR_NOT_CONVERGED (x still written) when max_iters is reached above tol.
+ */
+sme_status sme_lsqr(sme_op op, const void *u_bar, const void *v_bar, const void *b, void *x,
+                    const sme_lsqr_params *p, sme_lsqr_result *res, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SME_H */

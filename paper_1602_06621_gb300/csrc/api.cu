@@ -1,0 +1,232 @@
+// C ABI glue: error reporting, operator lifetime, status checks.
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "sme_internal.cuh"
+
+namespace sme {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+sme_status cuda_fail(cudaError_t e, const char *what, int line)
+{
+    set_error("CUDA error %d (%s) in %s at line %d", (int)e, cudaGetErrorString(e), what, line);
+    return e == cudaErrorMemoryAllocation ? SME_ERR_OOM : SME_ERR_CUDA;
+}
+
+sme_status dev_alloc(sme_op op, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        return SME_ERR_OOM;
+    }
+    op->device_bytes += (int64_t)bytes;
+    return SME_OK;
+}
+
+void dev_free(sme_op op, void *p, size_t bytes)
+{
+    if (!p) return;
+    cudaFree(p);
+    op->device_bytes -= (int64_t)(bytes == 0 ? 16 : bytes);
+}
+
+static void free_sell(sme_op op, Sell &S)
+{
+    for (void *p : {(void *)S.slice_off, (void *)S.slice_w, (void *)S.perm, (void *)S.iperm, (void *)S.len, S.ent,
+                    (void *)S.val64})
+        if (p) cudaFree(p);
+    S = Sell{};
+    (void)op;
+}
+
+// Host-side CSR validation (for host input), mirrors the device check.
+template <typename real>
+static sme_status validate_host(int64_t m, int64_t n, int64_t nnz, const int32_t *rp, const int32_t *col,
+                                const real *val)
+{
+    if (rp[0] != 0 || rp[m] != nnz) {
+        set_error("row_ptr must start at 0 and end at nnz");
+        return SME_ERR_INVALID_CSR;
+    }
+    for (int64_t i = 0; i < m; ++i) {
+        if (rp[i + 1] < rp[i]) {
+            set_error("row_ptr decreases at row %lld", (long long)i);
+            return SME_ERR_INVALID_CSR;
+        }
+        int32_t prev = -1;
+        for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
+            if (col[q] <= prev || col[q] >= n) {
+                set_error("column index out of range or not increasing in row %lld", (long long)i);
+                return SME_ERR_INVALID_CSR;
+            }
+            prev = col[q];
+            if (!std::isfinite((double)val[q])) {
+                set_error("non-finite value at nonzero %lld", (long long)q);
+                return SME_ERR_NONFINITE;
+            }
+        }
+    }
+    return SME_OK;
+}
+
+}  // namespace sme
+
+using namespace sme;
+
+extern "C" const char *sme_status_string(sme_status s)
+{
+    switch (s) {
+        case SME_OK: return "ok";
+        case SME_ERR_ARG: return "invalid argument";
+        case SME_ERR_INVALID_CSR: return "invalid CSR";
+        case SME_ERR_OOM: return "out of device memory";
+        case SME_ERR_CUDA: return "CUDA error";
+        case SME_ERR_NONFINITE: return "non-finite value";
+        case SME_ERR_TIMEOUT: return "device wait timed out";
+        case SME_ERR_NOT_CONVERGED: return "not converged";
+        case SME_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+extern "C" const char *sme_last_error(void) { return g_err; }
+
+extern "C" sme_status sme_op_destroy(sme_op op)
+{
+    if (!op) return SME_OK;
+    cudaDeviceSynchronize();
+    free_sell(op, op->fwd);
+    free_sell(op, op->bwd);
+    Workspace &W = op->ws;
+    for (void *p : {W.u, W.v, W.ub, W.vb, W.tab_u[0], W.tab_u[1], W.tab_v[0], W.tab_v[1], W.lsqr, (void *)W.red})
+        if (p) cudaFree(p);
+    release_lsqr(op);
+    if (op->graph.exec) cudaGraphExecDestroy(op->graph.exec);
+    if (op->dense) dense_destroy(op);
+    if (op->d_status) cudaFree(op->d_status);
+    delete op;
+    return SME_OK;
+}
+
+extern "C" sme_status sme_op_create_csr(sme_op *out, int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr,
+                                        const int32_t *col_idx, const void *vals, sme_dtype dtype, int on_device,
+                                        void *stream)
+{
+    if (!out) return SME_ERR_ARG;
+    *out = nullptr;
+    if (m < 1 || n < 1 || nnz < 0 || nnz > 0x7fffffffLL - 64 || m > 0x7fffffffLL || n > 0x7fffffffLL || !row_ptr ||
+        (nnz > 0 && (!col_idx || !vals))) {
+        set_error("sme_op_create_csr: bad sizes or null pointers");
+        return SME_ERR_ARG;
+    }
+    if (dtype != SME_F64 && dtype != SME_F32) {
+        set_error("sme_op_create_csr: dtype must be SME_F64 or SME_F32");
+        return SME_ERR_ARG;
+    }
+    const size_t vsz = dtype == SME_F64 ? 8 : 4;
+    if (!on_device) {
+        sme_status st = dtype == SME_F64
+                            ? validate_host<double>(m, n, nnz, row_ptr, col_idx, (const double *)vals)
+                            : validate_host<float>(m, n, nnz, row_ptr, col_idx, (const float *)vals);
+        if (st != SME_OK) return st;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    sme_op op = new sme_op_s();
+    op->m = m;
+    op->n = n;
+    op->nnz = nnz;
+    op->dtype = dtype;
+    op->dbl = dtype == SME_F64;
+    sme_status st = dev_alloc(op, (void **)&op->d_status, sizeof(int));
+    if (st != SME_OK) {
+        sme_op_destroy(op);
+        return st;
+    }
+    const int32_t *d_rp = row_ptr, *d_col = col_idx;
+    const void *d_val = vals;
+    void *tmp[3] = {nullptr, nullptr, nullptr};
+    if (!on_device) {
+        const size_t bytes[3] = {(size_t)(m + 1) * 4, (size_t)std::max<int64_t>(nnz, 1) * 4,
+                                 (size_t)std::max<int64_t>(nnz, 1) * vsz};
+        const void *src[3] = {row_ptr, col_idx, vals};
+        for (int i = 0; i < 3; ++i) {
+            if (cudaMalloc(&tmp[i], bytes[i]) != cudaSuccess) {
+                cudaGetLastError();
+                for (void *p : tmp)
+                    if (p) cudaFree(p);
+                sme_op_destroy(op);
+                set_error("sme_op_create_csr: staging allocation failed");
+                return SME_ERR_OOM;
+            }
+            if (i == 0 || nnz > 0) cudaMemcpyAsync(tmp[i], src[i], i == 0 ? bytes[0] : (size_t)nnz * (i == 1 ? 4 : vsz),
+                                                   cudaMemcpyHostToDevice, s);
+        }
+        d_rp = (const int32_t *)tmp[0];
+        d_col = (const int32_t *)tmp[1];
+        d_val = tmp[2];
+    }
+    st = build_sparse(op, d_rp, d_col, d_val, s);
+    cudaStreamSynchronize(s);
+    for (void *p : tmp)
+        if (p) cudaFree(p);
+    if (st != SME_OK) {
+        sme_op_destroy(op);
+        return st;
+    }
+    *out = op;
+    return SME_OK;
+}
+
+extern "C" sme_status sme_op_get_info(sme_op op, sme_op_info *info)
+{
+    if (!op || !info) return SME_ERR_ARG;
+    info->m = op->m;
+    info->n = op->n;
+    info->nnz = op->nnz;
+    info->dtype = (int32_t)op->dtype;
+    info->state_is_double = op->dbl ? 1 : 0;
+    info->device_bytes = op->device_bytes;
+    info->padded_entries_fwd = op->fwd.entries;
+    info->padded_entries_bwd = op->bwd.entries;
+    return SME_OK;
+}
+
+extern "C" sme_status sme_op_check(sme_op op, void *stream)
+{
+    if (!op) return SME_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = 0;
+    SME_CUDA(cudaMemcpyAsync(&st, op->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SME_CUDA(cudaStreamSynchronize(s));
+    if (st) SME_CUDA(cudaMemsetAsync(op->d_status, 0, sizeof(int), s));
+    if (st & ST_TIMEOUT) {
+        set_error("a device-side wait timed out");
+        return SME_ERR_TIMEOUT;
+    }
+    if (st & ST_NONFINITE) {
+        set_error("an iterate became non-finite");
+        return SME_ERR_NONFINITE;
+    }
+    return SME_OK;
+}

@@ -1,0 +1,487 @@
+// Algorithm 1 (projected stochastic gradient for eq. (3)) on the device.
+//
+// One launch performs one iteration t.  Its CTAs split into two groups:
+//   rows    (A, sliced ELL):    z_u[i] = (1/k) sum_p ( e^{u_i} sum_j A_ij e^{v_j} s_jp )^2
+//   columns (A^T, sliced ELL):  z_v[j] = (1/k) sum_p ( e^{v_j} sum_i A_ij e^{u_i} w_ip )^2
+// and every thread owns one row (one column), so the square-and-reduce over the
+// k probes, the projected step, the running average and the next iteration's
+// probe words all happen in registers right after the row's products.
+//
+// Both groups read the PREVIOUS iterate through double-buffered gather tables
+// (entry = { e^{x}, probe words }) and write the next table, so the u- and v-steps
+// of one iteration never see each other's new values (D and E are formed once
+// at the top of the iteration in Algorithm 1).
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "sme_internal.cuh"
+
+namespace sme {
+
+constexpr int ITER_THREADS = 256;
+constexpr int SLICES_PER_CTA = ITER_THREADS / 32;
+
+struct SellArgs {
+    const int64_t *slice_off;
+    const int32_t *slice_w;
+    const void *ent;
+    const double *val64;
+    const int32_t *perm;
+    int64_t rows, nslices;
+};
+
+template <typename real>
+struct StepArgs {
+    SellArgs A[2];          // [0] rows of A, [1] rows of A^T (columns of A)
+    const void *tab_in[2];  // [0] column table (read by rows), [1] row table (read by columns)
+    void *tab_out[2];       // [0] next row table (written by rows), [1] next column table
+    real *x[2];             // [0] u, [1] v, sorted order
+    real *xb[2];            // averages, sorted order
+    real *z[2];             // estimate-only outputs, original order
+    real target2[2];        // alpha^2, beta^2
+    real gamma, M, eta, avg_new, avg_old;
+    uint32_t t_next, key0, key1;
+    uint32_t sid_out[2];    // Philox stream of the table each side writes: rows -> w, columns -> s
+    int64_t blocks0;
+    int mode;               // 0: full step, 1: estimate only
+    int *status;
+};
+
+// ------------------------------------------------------------------ gather tables
+
+template <typename real, int KW>
+struct TabEntry;
+
+template <>
+struct TabEntry<float, 1> {
+    static constexpr int bytes = 8;
+    __device__ __forceinline__ static void load(const void *t, int32_t i, float &x, uint32_t (&w)[1])
+    {
+        const uint2 e = __ldg((const uint2 *)t + i);
+        x = __uint_as_float(e.x);
+        w[0] = e.y;
+    }
+    __device__ __forceinline__ static void store(void *t, int64_t i, float x, uint32_t w0, uint32_t)
+    {
+        ((uint2 *)t)[i] = make_uint2(__float_as_uint(x), w0);
+    }
+};
+
+template <>
+struct TabEntry<float, 2> {
+    static constexpr int bytes = 16;
+    __device__ __forceinline__ static void load(const void *t, int32_t i, float &x, uint32_t (&w)[2])
+    {
+        const uint4 e = __ldg((const uint4 *)t + i);
+        x = __uint_as_float(e.x);
+        w[0] = e.y;
+        w[1] = e.z;
+    }
+    __device__ __forceinline__ static void store(void *t, int64_t i, float x, uint32_t w0, uint32_t w1)
+    {
+        ((uint4 *)t)[i] = make_uint4(__float_as_uint(x), w0, w1, 0u);
+    }
+};
+
+template <int KW>
+struct TabEntry<double, KW> {
+    static constexpr int bytes = 16;
+    __device__ __forceinline__ static void load(const void *t, int32_t i, double &x, uint32_t (&w)[KW])
+    {
+        const uint4 e = __ldg((const uint4 *)t + i);
+        x = __hiloint2double((int)e.y, (int)e.x);
+        w[0] = e.z;
+        if (KW > 1) w[KW - 1] = e.w;
+    }
+    __device__ __forceinline__ static void store(void *t, int64_t i, double x, uint32_t w0, uint32_t w1)
+    {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+        ((uint4 *)t)[i] = make_uint4((uint32_t)b, (uint32_t)(b >> 32), w0, w1);
+    }
+};
+
+// ------------------------------------------------------------------ entries
+
+__device__ __forceinline__ void load_pair(const SellArgs &S, int64_t pi, int &c0, float &a0, int &c1, float &a1)
+{
+    const int4 e = __ldcs((const int4 *)S.ent + pi);
+    c0 = e.x;
+    a0 = __int_as_float(e.y);
+    c1 = e.z;
+    a1 = __int_as_float(e.w);
+}
+
+__device__ __forceinline__ void load_pair(const SellArgs &S, int64_t pi, int &c0, double &a0, int &c1, double &a1)
+{
+    const int2 c = __ldcs((const int2 *)S.ent + pi);
+    const double2 v = __ldcs((const double2 *)S.val64 + pi);
+    c0 = c.x;
+    c1 = c.y;
+    a0 = v.x;
+    a1 = v.y;
+}
+
+// acc[p] += (sign of probe p) * y, the sign being bit p of the probe words (set = -1).
+template <int K>
+__device__ __forceinline__ void acc_signed(float (&acc)[K], float y, const uint32_t *w)
+{
+    const uint32_t yb = __float_as_uint(y);
+#pragma unroll
+    for (int p = 0; p < K; ++p) {
+        const uint32_t sgn = (w[p >> 5] << (31 - (p & 31))) & 0x80000000u;
+        acc[p] += __uint_as_float(yb ^ sgn);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void acc_signed(double (&acc)[K], double y, const uint32_t *w)
+{
+#pragma unroll
+    for (int p = 0; p < K; ++p) {
+        const bool neg = (w[p >> 5] >> (p & 31)) & 1u;
+        acc[p] += neg ? -y : y;
+    }
+}
+
+__device__ __forceinline__ float dexp(float x) { return expf(x); }
+__device__ __forceinline__ double dexp(double x) { return exp(x); }
+__device__ __forceinline__ float dclip(float x, float M) { return fminf(fmaxf(x, -M), M); }
+__device__ __forceinline__ double dclip(double x, double M) { return fmin(fmax(x, -M), M); }
+
+// ------------------------------------------------------------------ the iteration kernel
+
+template <typename real, int K>
+__global__ void __launch_bounds__(ITER_THREADS) sgd_iteration(StepArgs<real> a)
+{
+    constexpr int KW = (K + 31) / 32;
+    using Tab = TabEntry<real, KW>;
+    // Select this CTA's side with per-field selects (no dynamic indexing into the parameter block).
+    const bool cols = (int64_t)blockIdx.x >= a.blocks0;
+    const int64_t blk = cols ? (int64_t)blockIdx.x - a.blocks0 : (int64_t)blockIdx.x;
+    const SellArgs S = cols ? a.A[1] : a.A[0];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t slice = blk * SLICES_PER_CTA + warp;
+    if (slice >= S.nslices) return;
+    const int64_t r = slice * 32 + lane;
+
+    real acc[K];
+#pragma unroll
+    for (int p = 0; p < K; ++p) acc[p] = real(0);
+
+    const int w = S.slice_w[slice];
+    const int64_t pbase = S.slice_off[slice] / 2 + lane;
+    const void *tab = cols ? a.tab_in[1] : a.tab_in[0];
+#pragma unroll 2
+    for (int q = 0; q < w / 2; ++q) {
+        int c0, c1;
+        real a0, a1;
+        load_pair(S, pbase + (int64_t)q * 32, c0, a0, c1, a1);
+        real x0, x1;
+        uint32_t w0[KW], w1[KW];
+        Tab::load(tab, c0, x0, w0);
+        Tab::load(tab, c1, x1, w1);
+        acc_signed<K>(acc, a0 * x0, w0);
+        acc_signed<K>(acc, a1 * x1, w1);
+    }
+    if (r >= S.rows) return;
+
+    real ss = real(0);
+#pragma unroll
+    for (int p = 0; p < K; ++p) ss += acc[p] * acc[p];
+    real *X = cols ? a.x[1] : a.x[0];
+    const real xo = X[r];
+    const real ex = dexp(xo);
+    const real z = ex * ex * ss * (real(1) / real(K));
+    if (a.mode == 1) {
+        (cols ? a.z[1] : a.z[0])[S.perm[r]] = z;
+        return;
+    }
+    real xn = xo - a.eta * (z - (cols ? a.target2[1] : a.target2[0]) + a.gamma * xo);
+    if (!isfinite(xn)) atomicOr(a.status, ST_NONFINITE);
+    xn = dclip(xn, a.M);
+    X[r] = xn;
+    real *XB = cols ? a.xb[1] : a.xb[0];
+    XB[r] = a.avg_new * xn + a.avg_old * XB[r];
+    uint32_t pw0, pw1;
+    probe_words2((uint32_t)S.perm[r], a.t_next, cols ? a.sid_out[1] : a.sid_out[0], a.key0, a.key1, pw0, pw1);
+    Tab::store(cols ? a.tab_out[1] : a.tab_out[0], r, dexp(xn), pw0, pw1);
+}
+
+// Load a start state (original order) into sorted order and build the tables of iteration t.
+template <typename real, int KW>
+__global__ void load_state(int64_t rows, const int32_t *perm, const real *x_in, const real *xb_in, real *x,
+                           real *xb, void *tab, uint32_t t, uint32_t sid, uint32_t k0, uint32_t k1)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const int32_t i = perm[r];
+    const real xi = x_in ? x_in[i] : real(0);
+    if (x) x[r] = xi;
+    if (xb) xb[r] = xb_in ? xb_in[i] : real(0);
+    uint32_t w0, w1;
+    probe_words2((uint32_t)i, t, sid, k0, k1, w0, w1);
+    TabEntry<real, KW>::store(tab, r, dexp(xi), w0, w1);
+}
+
+template <typename real>
+__global__ void store_state(int64_t rows, const int32_t *perm, const real *x, const real *xb, real *x_out,
+                            real *xb_out)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const int32_t i = perm[r];
+    x_out[i] = x[r];
+    xb_out[i] = xb[r];
+}
+
+__global__ void draw_probe_words(uint64_t seed, uint32_t t, uint32_t sid, int64_t len, int kw, uint32_t *out)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= len) return;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int w = 0; w < kw; w += 4) {
+        const U4 o = philox10(U4{(uint32_t)idx, t, sid, (uint32_t)(w >> 2)}, k0, k1);
+        const uint32_t ws[4] = {o.x, o.y, o.z, o.w};
+        for (int h = 0; h < 4 && w + h < kw; ++h) out[(int64_t)(w + h) * len + idx] = ws[h];
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+static bool k_supported(int k) { return k == 1 || k == 2 || k == 4 || k == 8 || k == 16 || k == 32 || k == 64; }
+
+static int entry_bytes(bool dbl, int kw) { return (!dbl && kw == 1) ? 8 : 16; }
+
+sme_status ensure_equil_workspace(sme_op op, int kw)
+{
+    Workspace &W = op->ws;
+    const size_t sz = op->dbl ? 8 : 4;
+    if (!W.u) {
+        SME_TRY(dev_alloc(op, &W.u, op->m * sz));
+        SME_TRY(dev_alloc(op, &W.ub, op->m * sz));
+        SME_TRY(dev_alloc(op, &W.v, op->n * sz));
+        SME_TRY(dev_alloc(op, &W.vb, op->n * sz));
+    }
+    const int64_t eb = entry_bytes(op->dbl, kw);
+    const int64_t need_u = op->fwd.nslices * 32 * eb, need_v = op->bwd.nslices * 32 * eb;
+    if (W.tab_bytes_u < need_u) {
+        for (int b = 0; b < 2; ++b) {
+            dev_free(op, W.tab_u[b], W.tab_bytes_u);
+            W.tab_u[b] = nullptr;
+            SME_TRY(dev_alloc(op, &W.tab_u[b], need_u));
+        }
+        W.tab_bytes_u = need_u;
+    }
+    if (W.tab_bytes_v < need_v) {
+        for (int b = 0; b < 2; ++b) {
+            dev_free(op, W.tab_v[b], W.tab_bytes_v);
+            W.tab_v[b] = nullptr;
+            SME_TRY(dev_alloc(op, &W.tab_v[b], need_v));
+        }
+        W.tab_bytes_v = need_v;
+    }
+    return SME_OK;
+}
+
+static SellArgs sell_args(const Sell &S)
+{
+    return SellArgs{S.slice_off, S.slice_w, S.ent, S.val64, S.perm, S.rows, S.nslices};
+}
+
+template <typename real>
+static void launch_iteration(const StepArgs<real> &a, int k, unsigned grid, cudaStream_t s)
+{
+    switch (k) {
+        case 1: sgd_iteration<real, 1><<<grid, ITER_THREADS, 0, s>>>(a); break;
+        case 2: sgd_iteration<real, 2><<<grid, ITER_THREADS, 0, s>>>(a); break;
+        case 4: sgd_iteration<real, 4><<<grid, ITER_THREADS, 0, s>>>(a); break;
+        case 8: sgd_iteration<real, 8><<<grid, ITER_THREADS, 0, s>>>(a); break;
+        case 16: sgd_iteration<real, 16><<<grid, ITER_THREADS, 0, s>>>(a); break;
+        case 32: sgd_iteration<real, 32><<<grid, ITER_THREADS, 0, s>>>(a); break;
+        case 64: sgd_iteration<real, 64><<<grid, ITER_THREADS, 0, s>>>(a); break;
+        default: break;
+    }
+}
+
+template <typename real>
+static void launch_load(sme_op op, int side, int kw, const real *x_in, const real *xb_in, real *x, real *xb,
+                        void *tab, uint32_t t, uint32_t sid, uint64_t seed, cudaStream_t s)
+{
+    const Sell &S = side == 0 ? op->fwd : op->bwd;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    if (op->dbl || kw == 2)
+        load_state<real, 2><<<nblk(S.rows), 256, 0, s>>>(S.rows, S.perm, x_in, xb_in, x, xb, tab, t, sid, k0, k1);
+    else
+        load_state<real, 1><<<nblk(S.rows), 256, 0, s>>>(S.rows, S.perm, x_in, xb_in, x, xb, tab, t, sid, k0, k1);
+}
+
+struct Resolved {
+    double alpha, beta, gamma, M;
+};
+
+static Resolved resolve(sme_op op, double alpha, double beta, double gamma, double M)
+{
+    Resolved r;
+    r.alpha = alpha > 0 ? alpha : std::pow((double)op->n / (double)op->m, 0.25);
+    r.beta = beta > 0 ? beta : std::pow((double)op->m / (double)op->n, 0.25);
+    r.gamma = gamma > 0 ? gamma : 0.1;
+    r.M = M > 0 ? M : std::log(1e4);
+    return r;
+}
+
+template <typename real>
+static StepArgs<real> base_args(sme_op op, int buf_in, const Resolved &R, uint64_t seed)
+{
+    StepArgs<real> a{};
+    a.A[0] = sell_args(op->fwd);
+    a.A[1] = sell_args(op->bwd);
+    a.tab_in[0] = op->ws.tab_v[buf_in];
+    a.tab_in[1] = op->ws.tab_u[buf_in];
+    a.tab_out[0] = op->ws.tab_u[buf_in ^ 1];
+    a.tab_out[1] = op->ws.tab_v[buf_in ^ 1];
+    a.x[0] = (real *)op->ws.u;
+    a.x[1] = (real *)op->ws.v;
+    a.xb[0] = (real *)op->ws.ub;
+    a.xb[1] = (real *)op->ws.vb;
+    a.target2[0] = (real)(R.alpha * R.alpha);
+    a.target2[1] = (real)(R.beta * R.beta);
+    a.gamma = (real)R.gamma;
+    a.M = (real)R.M;
+    a.key0 = (uint32_t)seed;
+    a.key1 = (uint32_t)(seed >> 32);
+    a.blocks0 = (op->fwd.nslices + SLICES_PER_CTA - 1) / SLICES_PER_CTA;
+    a.status = op->d_status;
+    return a;
+}
+
+static unsigned iter_grid(sme_op op)
+{
+    return (unsigned)((op->fwd.nslices + SLICES_PER_CTA - 1) / SLICES_PER_CTA +
+                      (op->bwd.nslices + SLICES_PER_CTA - 1) / SLICES_PER_CTA);
+}
+
+template <typename real>
+static sme_status equilibrate_t(sme_op op, const sme_equil_params *p, real *u, real *v, real *ub, real *vb,
+                                cudaStream_t s)
+{
+    const int k = p->k, kw = (k + 31) / 32;
+    SME_TRY(ensure_equil_workspace(op, kw));
+    const Resolved R = resolve(op, p->alpha, p->beta, p->gamma, p->M);
+    const uint32_t sid_s = (uint32_t)p->stream_base, sid_w = (uint32_t)p->stream_base + 1u;
+    const int tb = p->t_begin;
+    int buf = tb & 1;
+    launch_load<real>(op, 0, kw, u, ub, (real *)op->ws.u, (real *)op->ws.ub, op->ws.tab_u[buf], (uint32_t)tb, sid_w,
+                      p->seed, s);
+    launch_load<real>(op, 1, kw, v, vb, (real *)op->ws.v, (real *)op->ws.vb, op->ws.tab_v[buf], (uint32_t)tb, sid_s,
+                      p->seed, s);
+    const unsigned grid = iter_grid(op);
+    for (int t = tb; t < tb + p->T; ++t) {
+        StepArgs<real> a = base_args<real>(op, t & 1, R, p->seed);
+        a.eta = (real)(2.0 / (R.gamma * ((double)t + (double)p->t0 + 1.0)));
+        a.avg_new = (real)(2.0 / ((double)t + 2.0));
+        a.avg_old = (real)((double)t / ((double)t + 2.0));
+        a.t_next = (uint32_t)(t + 1);
+        a.sid_out[0] = sid_w;
+        a.sid_out[1] = sid_s;
+        a.mode = 0;
+        launch_iteration<real>(a, k, grid, s);
+    }
+    store_state<real><<<nblk(op->m), 256, 0, s>>>(op->m, op->fwd.perm, (real *)op->ws.u, (real *)op->ws.ub, u, ub);
+    store_state<real><<<nblk(op->n), 256, 0, s>>>(op->n, op->bwd.perm, (real *)op->ws.v, (real *)op->ws.vb, v, vb);
+    SME_CUDA(cudaGetLastError());
+    return SME_OK;
+}
+
+template <typename real>
+static sme_status estimate_t(sme_op op, const real *u, const real *v, int t, int k, uint64_t seed, int sb,
+                             real *zu, real *zv, cudaStream_t s)
+{
+    const int kw = (k + 31) / 32;
+    SME_TRY(ensure_equil_workspace(op, kw));
+    const Resolved R = resolve(op, 0, 0, 0, 0);
+    const int buf = 0;
+    launch_load<real>(op, 0, kw, u, nullptr, (real *)op->ws.u, nullptr, op->ws.tab_u[buf], (uint32_t)t,
+                      (uint32_t)sb + 1u, seed, s);
+    launch_load<real>(op, 1, kw, v, nullptr, (real *)op->ws.v, nullptr, op->ws.tab_v[buf], (uint32_t)t, (uint32_t)sb,
+                      seed, s);
+    StepArgs<real> a = base_args<real>(op, buf, R, seed);
+    a.mode = 1;
+    a.z[0] = zu;
+    a.z[1] = zv;
+    // A NULL output skips that side by giving it no slices.
+    if (!zu) a.A[0].nslices = 0;
+    if (!zv) a.A[1].nslices = 0;
+    launch_iteration<real>(a, k, iter_grid(op), s);
+    SME_CUDA(cudaGetLastError());
+    return SME_OK;
+}
+
+}  // namespace sme
+
+using namespace sme;
+
+extern "C" sme_status sme_draw_probes(uint64_t seed, int32_t t, int32_t stream_id, int64_t len, int32_t k,
+                                      uint32_t *words, void *stream)
+{
+    if (len < 0 || k < 1 || (len > 0 && !words)) {
+        set_error("sme_draw_probes: bad arguments");
+        return SME_ERR_ARG;
+    }
+    if (len == 0) return SME_OK;
+    draw_probe_words<<<nblk(len), 256, 0, (cudaStream_t)stream>>>(seed, (uint32_t)t, (uint32_t)stream_id, len,
+                                                                  (k + 31) / 32, words);
+    SME_CUDA(cudaGetLastError());
+    return SME_OK;
+}
+
+extern "C" sme_status sme_equilibrate(sme_op op, const sme_equil_params *p, void *u, void *v, void *u_bar,
+                                      void *v_bar, void *stream)
+{
+    if (!op || !p || !u || !v || !u_bar || !v_bar || p->T < 0 || p->t_begin < 1 || p->t0 < 0) {
+        set_error("sme_equilibrate: bad arguments");
+        return SME_ERR_ARG;
+    }
+    if (!k_supported(p->k)) {
+        set_error("sme_equilibrate: k=%d not supported (1,2,4,...,64)", p->k);
+        return SME_ERR_UNSUPPORTED;
+    }
+    if (op->dense) {
+        SME_TRY(dense_equilibrate(op, p, (float *)u, (float *)v, (float *)u_bar, (float *)v_bar,
+                                  (cudaStream_t)stream));
+    } else if (op->dbl) {
+        SME_TRY(equilibrate_t<double>(op, p, (double *)u, (double *)v, (double *)u_bar, (double *)v_bar,
+                                      (cudaStream_t)stream));
+    } else {
+        SME_TRY(equilibrate_t<float>(op, p, (float *)u, (float *)v, (float *)u_bar, (float *)v_bar,
+                                     (cudaStream_t)stream));
+    }
+    if (p->flags & SME_EQ_ASYNC) return SME_OK;
+    return sme_op_check(op, stream);
+}
+
+extern "C" sme_status sme_estimate(sme_op op, const void *u, const void *v, int32_t t, int32_t k, uint64_t seed,
+                                   int32_t stream_base, void *z_u, void *z_v, void *stream)
+{
+    if (!op || !u || !v || t < 0) {
+        set_error("sme_estimate: bad arguments");
+        return SME_ERR_ARG;
+    }
+    if (!k_supported(k)) {
+        set_error("sme_estimate: k=%d not supported", k);
+        return SME_ERR_UNSUPPORTED;
+    }
+    if (op->dense) {
+        return dense_estimate(op, (const float *)u, (const float *)v, t, k, seed, stream_base, (float *)z_u,
+                              (float *)z_v, (cudaStream_t)stream);
+    }
+    if (op->dbl)
+        return estimate_t<double>(op, (const double *)u, (const double *)v, t, k, seed, stream_base, (double *)z_u,
+                                  (double *)z_v, (cudaStream_t)stream);
+    return estimate_t<float>(op, (const float *)u, (const float *)v, t, k, seed, stream_base, (float *)z_u,
+                             (float *)z_v, (cudaStream_t)stream);
+}

@@ -1,0 +1,175 @@
+// Internal declarations shared by the CUDA translation units of libsme.
+// Nothing here is part of the C ABI (see include/sme.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "sme.h"
+
+namespace sme {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const char *fmt, ...);
+sme_status cuda_fail(cudaError_t e, const char *what, int line);
+
+#define SME_CUDA(call)                                                     \
+    do {                                                                   \
+        cudaError_t _e = (call);                                           \
+        if (_e != cudaSuccess) return ::sme::cuda_fail(_e, #call, __LINE__); \
+    } while (0)
+
+#define SME_TRY(call)                        \
+    do {                                     \
+        sme_status _s = (call);              \
+        if (_s != SME_OK) return _s;         \
+    } while (0)
+
+// Device status word bits (set by kernels, read by sme_op_check).
+enum : int {
+    ST_NONFINITE = 1,
+    ST_BAD_CSR = 2,
+    ST_BAD_VALUE = 4,
+    ST_TIMEOUT = 8,
+};
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Counter-based generator of Salmon, Moraes, Dror & Shaw (SC'11): ten rounds of
+// two 32x32->64 multiplies with a Weyl-sequence key schedule.
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__host__ __device__ __forceinline__ void mulhilo32(uint32_t a, uint32_t b, uint32_t &hi, uint32_t &lo)
+{
+#if defined(__CUDA_ARCH__)
+    lo = a * b;
+    hi = __umulhi(a, b);
+#else
+    uint64_t p = (uint64_t)a * (uint64_t)b;
+    lo = (uint32_t)p;
+    hi = (uint32_t)(p >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t h0, l0, h1, l1;
+        mulhilo32(0xD2511F53u, c.x, h0, l0);
+        mulhilo32(0xCD9E8D57u, c.z, h1, l1);
+        c = U4{h1 ^ c.y ^ k0, l1, h0 ^ c.w ^ k1, l0};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// First two 32-bit probe words (probes 0..63) at `index` for iteration t and Philox stream `sid`.
+__host__ __device__ __forceinline__ void probe_words2(uint32_t index, uint32_t t, uint32_t sid, uint32_t k0,
+                                                      uint32_t k1, uint32_t &w0, uint32_t &w1)
+{
+    U4 o = philox10(U4{index, t, sid, 0u}, k0, k1);
+    w0 = o.x;
+    w1 = o.y;
+}
+
+// ------------------------------------------------------------------ operator
+
+// Sliced ELL with 32-row slices, rows in descending-length order ("sorted position").
+// Entries of slice s are stored in pairs of consecutive steps so that one 16-byte
+// load serves two steps of one row:
+//   pair q of lane r of slice s  ->  pair index slice_off[s]/2 + q*32 + r
+// FP32: int4 {col0, val0_bits, col1, val1_bits};  FP64: int2 {col0, col1} + double2 {val0, val1}.
+// Column (row) indices stored are SORTED positions of the other dimension.
+struct Sell {
+    int64_t rows = 0;       // logical rows (m for A, n for A^T)
+    int64_t nslices = 0;
+    int64_t entries = 0;    // incl. padding
+    int64_t *slice_off = nullptr;  // [nslices + 1], entry offsets (multiples of 64)
+    int32_t *slice_w = nullptr;    // [nslices], even widths
+    int32_t *perm = nullptr;       // sorted position -> original index
+    int32_t *iperm = nullptr;      // original index -> sorted position
+    int32_t *len = nullptr;        // [rows] length at each sorted position
+    void *ent = nullptr;           // see above
+    double *val64 = nullptr;       // FP64 values (double2 pairs), FP64 ops only
+};
+
+struct Workspace {
+    // Equilibration state in sorted order and the double-buffered gather tables.
+    void *u = nullptr, *v = nullptr, *ub = nullptr, *vb = nullptr;
+    void *tab_u[2] = {nullptr, nullptr};
+    void *tab_v[2] = {nullptr, nullptr};
+    int64_t tab_bytes_u = 0, tab_bytes_v = 0;
+    // LSQR vectors and FP64 reduction scratch.
+    void *lsqr = nullptr;
+    int64_t lsqr_bytes = 0;
+    double *red = nullptr;
+    int64_t red_len = 0;
+};
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t stream = nullptr;
+    int64_t key[12] = {0};
+};
+
+struct DenseOp;  // tensor-core operator (dense A)
+
+}  // namespace sme
+
+struct sme_op_s {
+    int64_t m = 0, n = 0, nnz = 0;
+    sme_dtype dtype = SME_F32;
+    bool dbl = false;  // state vectors in double
+    sme::Sell fwd, bwd;
+    sme::Workspace ws;
+    sme::GraphCache graph;
+    sme::DenseOp *dense = nullptr;
+    int *d_status = nullptr;
+    int64_t device_bytes = 0;
+};
+
+namespace sme {
+
+// Device allocation bookkeeping for an op.
+sme_status dev_alloc(sme_op op, void **p, size_t bytes);
+void dev_free(sme_op op, void *p, size_t bytes);
+
+// Build-time device utilities (build_kernels.cu).
+sme_status scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);  // out[n] = total
+sme_status scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);  // out[n] = total
+sme_status radix_sort_pairs(uint32_t *keys, int32_t *vals, uint32_t *keys_alt, int32_t *vals_alt, int64_t n,
+                            int key_bits, cudaStream_t s, bool *result_in_alt);
+sme_status build_sparse(sme_op op, const int32_t *d_row_ptr, const int32_t *d_col, const void *d_vals,
+                        cudaStream_t s);
+
+// Equilibration / estimation launches (equilibrate.cu).
+sme_status ensure_equil_workspace(sme_op op, int kw);
+
+// LSQR and evaluation (lsqr.cu).
+void release_lsqr(sme_op op);
+
+// Dense tensor-core operator (dense.cu).
+void dense_destroy(sme_op op);
+sme_status dense_equilibrate(sme_op op, const sme_equil_params *p, float *u, float *v, float *ub, float *vb,
+                             cudaStream_t s);
+sme_status dense_estimate(sme_op op, const float *u, const float *v, int t, int k, uint64_t seed, int sb,
+                          float *zu, float *zv, cudaStream_t s);
+
+inline int bit_length(uint64_t x)
+{
+    int b = 0;
+    while (x) {
+        ++b;
+        x >>= 1;
+    }
+    return b;
+}
+
+}  // namespace sme

@@ -98,11 +98,17 @@ def _distinct_columns_per_row(rng: np.random.Generator, m: int, n: int, lens: np
         raise ValueError("row length exceeds n")
     cols = rng.integers(0, n, size=(m, lmax), dtype=np.int64)
     mask = np.arange(lmax)[None, :] < lens[:, None]
-    # Redraw rows holding a repeated column among their first lens[i] slots until none remain.
+    # Rows long enough that a repeat is likely (lens^2 > n / 4) draw without replacement directly;
+    # the others redraw until no column repeats among their first lens[i] slots.
+    crowded = np.nonzero(lens * lens * 4 > n)[0]
+    for i in crowded:
+        cols[i, : lens[i]] = rng.choice(n, size=int(lens[i]), replace=False)
+    sparse_rows = np.ones(m, dtype=bool)
+    sparse_rows[crowded] = False
     while True:
         masked = np.where(mask, cols, -1 - np.arange(lmax)[None, :])
         s = np.sort(masked, axis=1)
-        dup = np.any((s[:, 1:] == s[:, :-1]) & (s[:, 1:] >= 0), axis=1)
+        dup = np.any((s[:, 1:] == s[:, :-1]) & (s[:, 1:] >= 0), axis=1) & sparse_rows
         bad = np.nonzero(dup)[0]
         if bad.size == 0:
             break

@@ -1,0 +1,213 @@
+"""Thin Python binding of libsme (include/sme.h): same names, argument marshalling only.
+
+Vectors are torch CUDA tensors (float64 for an SME_F64 operator, float32 otherwise);
+CSR input may be host NumPy arrays or CUDA tensors.  Every function raises
+SmeError on a non-OK status.  There is no fallback: if the CUDA library cannot be
+built or loaded, importing the functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB, build_library
+
+__all__ = [
+    "SmeError", "load", "SME_F64", "SME_F32", "SME_BF16", "SME_FP8E4M3", "SME_EQ_ASYNC", "SME_EQ_NO_GRAPH",
+    "sme_op_create_csr", "sme_op_create_dense", "sme_op_destroy", "sme_op_get_info", "sme_draw_probes",
+    "sme_equilibrate", "sme_op_check", "sme_estimate", "sme_evaluate", "sme_lsqr", "sme_status_string",
+    "default_params",
+]
+
+SME_F64, SME_F32, SME_BF16, SME_FP8E4M3 = 0, 1, 2, 3
+SME_EQ_ASYNC, SME_EQ_NO_GRAPH = 1, 2
+_STATUS = {0: "SME_OK", -1: "SME_ERR_ARG", -2: "SME_ERR_INVALID_CSR", -3: "SME_ERR_OOM", -4: "SME_ERR_CUDA",
+           -5: "SME_ERR_NONFINITE", -6: "SME_ERR_TIMEOUT", -7: "SME_ERR_NOT_CONVERGED", -8: "SME_ERR_UNSUPPORTED"}
+
+
+class SmeError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)} ({detail})")
+        self.status = status
+        self.name = _STATUS.get(status, str(status))
+
+
+class sme_equil_params(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("M", ctypes.c_double), ("T", ctypes.c_int32), ("k", ctypes.c_int32), ("t_begin", ctypes.c_int32),
+                ("t0", ctypes.c_int32), ("seed", ctypes.c_uint64), ("stream_base", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+class sme_op_info(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("state_is_double", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+                ("padded_entries_fwd", ctypes.c_int64), ("padded_entries_bwd", ctypes.c_int64)]
+
+
+class sme_eval_result(ctypes.Structure):
+    _fields_ = [("row_spread", ctypes.c_double), ("col_spread", ctypes.c_double), ("rms", ctypes.c_double),
+                ("objective", ctypes.c_double), ("empty_rows", ctypes.c_int64), ("empty_cols", ctypes.c_int64)]
+
+
+class sme_lsqr_params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int64), ("check_every", ctypes.c_int32),
+                ("stop_rule", ctypes.c_int32)]
+
+
+class sme_lsqr_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("rel_residual", ctypes.c_double), ("normal_residual", ctypes.c_double),
+                ("converged", ctypes.c_int32)]
+
+
+_lib = None
+_vp, _i64, _i32, _u64, _d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double
+
+# Exported symbols and their argument types (kept in step with include/sme.h).
+SIGNATURES = {
+    "sme_status_string": ([_i32], ctypes.c_char_p),
+    "sme_last_error": ([], ctypes.c_char_p),
+    "sme_op_create_csr": ([ctypes.POINTER(_vp), _i64, _i64, _i64, _vp, _vp, _vp, _i32, _i32, _vp], _i32),
+    "sme_op_create_dense": ([ctypes.POINTER(_vp), _i64, _i64, _vp, _i64, _i32, _vp, _i32, _vp], _i32),
+    "sme_op_destroy": ([_vp], _i32),
+    "sme_op_get_info": ([_vp, ctypes.POINTER(sme_op_info)], _i32),
+    "sme_draw_probes": ([_u64, _i32, _i32, _i64, _i32, _vp, _vp], _i32),
+    "sme_equilibrate": ([_vp, ctypes.POINTER(sme_equil_params), _vp, _vp, _vp, _vp, _vp], _i32),
+    "sme_op_check": ([_vp, _vp], _i32),
+    "sme_estimate": ([_vp, _vp, _vp, _i32, _i32, _u64, _i32, _vp, _vp, _vp], _i32),
+    "sme_evaluate": ([_vp, _vp, _vp, _d, _d, _d, _vp, _vp, ctypes.POINTER(sme_eval_result), _vp], _i32),
+    "sme_lsqr": ([_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(sme_lsqr_params), ctypes.POINTER(sme_lsqr_result), _vp],
+                 _i32),
+}
+
+
+def load(build: bool = True):
+    """Load libsme.so, building it first when sources are newer.  Raises if it cannot be loaded."""
+    global _lib
+    if _lib is None:
+        path = build_library() if build else LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libsme.so not found at {path}; run paper_1602_06621_gb300.build")
+        L = ctypes.CDLL(path)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise SmeError(st, where, load().sme_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def sme_status_string(status: int) -> str:
+    return load().sme_status_string(status).decode()
+
+
+def default_params(m: int, n: int) -> dict:
+    """Section 4 parameters: alpha=(n/m)^(1/4), beta=(m/n)^(1/4), gamma=0.1, M=log(1e4)."""
+    import math
+    return dict(alpha=(n / m) ** 0.25, beta=(m / n) ** 0.25, gamma=0.1, M=math.log(1e4))
+
+
+def sme_op_create_csr(m, n, row_ptr, col_idx, vals, dtype=None, stream=None):
+    """Create a sparse operator.  Host NumPy arrays are copied; CUDA tensors are read in place."""
+    on_device = not isinstance(row_ptr, np.ndarray)
+    if on_device:
+        import torch
+        if dtype is None:
+            dtype = SME_F64 if vals.dtype == torch.float64 else SME_F32
+        nnz = int(col_idx.numel())
+    else:
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+        if dtype is None:
+            dtype = SME_F64 if vals.dtype == np.float64 else SME_F32
+        vals = np.ascontiguousarray(vals, dtype=np.float64 if dtype == SME_F64 else np.float32)
+        nnz = int(col_idx.size)
+    op = ctypes.c_void_p()
+    st = load().sme_op_create_csr(ctypes.byref(op), int(m), int(n), nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(vals),
+                                  int(dtype), int(on_device), _stream(stream))
+    _check(st, "sme_op_create_csr")
+    return op
+
+
+def sme_op_create_dense(m, n, A, lda=None, dtype=SME_BF16, row_scales=None, stream=None):
+    on_device = not isinstance(A, np.ndarray)
+    op = ctypes.c_void_p()
+    st = load().sme_op_create_dense(ctypes.byref(op), int(m), int(n), _ptr(A), int(lda if lda else n), int(dtype),
+                                    _ptr(row_scales), int(on_device), _stream(stream))
+    _check(st, "sme_op_create_dense")
+    return op
+
+
+def sme_op_destroy(op):
+    if op:
+        _check(load().sme_op_destroy(op), "sme_op_destroy")
+
+
+def sme_op_get_info(op) -> dict:
+    info = sme_op_info()
+    _check(load().sme_op_get_info(op, ctypes.byref(info)), "sme_op_get_info")
+    return {f: getattr(info, f) for f, _ in sme_op_info._fields_}
+
+
+def sme_draw_probes(seed, t, stream_id, length, k, words, stream=None):
+    _check(load().sme_draw_probes(int(seed), int(t), int(stream_id), int(length), int(k), _ptr(words),
+                                  _stream(stream)), "sme_draw_probes")
+
+
+def sme_equilibrate(op, u, v, u_bar, v_bar, *, T, k, t_begin=1, t0=0, seed=0, stream_base=0, alpha=0.0,
+                    beta=0.0, gamma=0.0, M=0.0, flags=0, stream=None):
+    p = sme_equil_params(alpha, beta, gamma, M, int(T), int(k), int(t_begin), int(t0), int(seed), int(stream_base),
+                         int(flags))
+    _check(load().sme_equilibrate(op, ctypes.byref(p), _ptr(u), _ptr(v), _ptr(u_bar), _ptr(v_bar), _stream(stream)),
+           "sme_equilibrate")
+
+
+def sme_op_check(op, stream=None):
+    _check(load().sme_op_check(op, _stream(stream)), "sme_op_check")
+
+
+def sme_estimate(op, u, v, t, k, seed, stream_base, z_u, z_v, stream=None):
+    _check(load().sme_estimate(op, _ptr(u), _ptr(v), int(t), int(k), int(seed), int(stream_base), _ptr(z_u),
+                               _ptr(z_v), _stream(stream)), "sme_estimate")
+
+
+def sme_evaluate(op, u, v, alpha=0.0, beta=0.0, gamma=0.0, r2=None, c2=None, stream=None) -> dict:
+    res = sme_eval_result()
+    _check(load().sme_evaluate(op, _ptr(u), _ptr(v), float(alpha), float(beta), float(gamma), _ptr(r2), _ptr(c2),
+                               ctypes.byref(res), _stream(stream)), "sme_evaluate")
+    return {f: getattr(res, f) for f, _ in sme_eval_result._fields_}
+
+
+def sme_lsqr(op, u_bar, v_bar, b, x, *, tol=1e-6, max_iters=100000, check_every=10, stop_rule=0, stream=None,
+             raise_on_not_converged=False) -> dict:
+    p = sme_lsqr_params(float(tol), int(max_iters), int(check_every), int(stop_rule))
+    res = sme_lsqr_result()
+    st = load().sme_lsqr(op, _ptr(u_bar), _ptr(v_bar), _ptr(b), _ptr(x), ctypes.byref(p), ctypes.byref(res),
+                         _stream(stream))
+    if st != -7 or raise_on_not_converged:
+        _check(st, "sme_lsqr")
+    return {f: getattr(res, f) for f, _ in sme_lsqr_result._fields_}

@@ -1,0 +1,70 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol include/sme.h declares.
+Host-side argument and CSR validation returns its status codes before any device work,
+so those paths are checked here without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1602_06621_gb300 import sme
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(sme_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = sme.load()
+    names = _declared()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in sme.SIGNATURES, f"binding lacks {name}"
+
+
+def test_status_strings():
+    assert sme.sme_status_string(0) == "ok"
+    assert sme.sme_status_string(-2) == "invalid CSR"
+
+
+def _csr():
+    rp = np.array([0, 2, 3, 5], np.int32)
+    col = np.array([0, 2, 1, 0, 3], np.int32)
+    val = np.array([1.0, -2.0, 3.0, 0.5, 4.0])
+    return rp, col, val
+
+
+@pytest.mark.parametrize("mutate,code", [
+    (lambda rp, col, val: rp.__setitem__(1, 4), "SME_ERR_INVALID_CSR"),        # row_ptr decreases
+    (lambda rp, col, val: col.__setitem__(4, 9), "SME_ERR_INVALID_CSR"),       # column out of range
+    (lambda rp, col, val: col.__setitem__(1, 0), "SME_ERR_INVALID_CSR"),       # repeated column
+    (lambda rp, col, val: rp.__setitem__(3, 4), "SME_ERR_INVALID_CSR"),        # row_ptr[m] != nnz
+    (lambda rp, col, val: val.__setitem__(2, np.nan), "SME_ERR_NONFINITE"),    # NaN value
+    (lambda rp, col, val: val.__setitem__(0, np.inf), "SME_ERR_NONFINITE"),    # Inf value
+])
+def test_host_csr_validation(mutate, code):
+    rp, col, val = _csr()
+    mutate(rp, col, val)
+    with pytest.raises(sme.SmeError) as ei:
+        sme.sme_op_create_csr(3, 4, rp, col, val, stream=0)
+    assert ei.value.name == code
+
+
+def test_degenerate_shapes_are_rejected():
+    rp, col, val = _csr()
+    with pytest.raises(sme.SmeError) as ei:
+        sme.sme_op_create_csr(0, 4, np.zeros(1, np.int32), col[:0], val[:0], stream=0)
+    assert ei.value.name == "SME_ERR_ARG"
+    lib = sme.load()
+    p = sme.sme_equil_params(0, 0, 0, 0, 10, 32, 1, 0, 0, 0, 0)
+    assert lib.sme_equilibrate(None, ctypes.byref(p), None, None, None, None, None) == -1
