@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""Benchmark of stochastic matrix-free equilibration on one node.
+
+A step is one pass of the hot path over the large sparse workload
+(1e6 x 5e5, 20 uniform-random nonzeros per row, FP32 values N(0,1) e^{r_i} e^{c_j}
+with r, c of variance 2): T = 500 iterations of Algorithm 1 with k = 32 probes per
+iteration from the zero start, then LSQR on the equilibrated operator to a
+relative residual of 1e-6 (checked in FP64 on the original system).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 is launched by torchrun, one rank per GPU; every rank equilibrates its own
+independent matrix (weak scaling, no data-path collective).  The reference arm
+(--impl reference) times the FP64 CPU oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "equilibration probe-pairs/s + HBM GB/s; time to LSQR 1e-6 vs plain, 1×GB300"
+UNIT = "probe-pairs/s"
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1602_06621_gb300", "csrc", "equilibrate.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sgd_iteration_f32_k32_large.txt")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink the workload (for quick runs only)")
+    ap.add_argument("--T", type=int, default=500)
+    ap.add_argument("--k", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-lsqr", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(A, k, T):
+    return (f"large sparse plain path: CSR A m={A.m} n={A.n} nnz={A.nnz} (20 per row, uniform-random columns), "
+            f"FP32 values N(0,1)*exp(N(0,2)) row and column factors; k={k} probes per iteration, T={T}; "
+            f"then LSQR (FP32 vectors, FP64 scalars) on D A E to ||Ax-b||/||b|| <= 1e-6, b = A x*")
+
+
+def algorithmic_bytes_per_iteration(m, n, nnz):
+    """Both passes read every nonzero (int32 index + FP32 value); u, ubar, v, vbar are each read and written."""
+    return 2 * nnz * 8 + 4 * 4 * (m + n)
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic():
+    """ncu DRAM bytes per launch of the iteration kernel, if taken on the current kernel source."""
+    try:
+        src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+        vals = {}
+        for line in open(TRAFFIC_FILE):
+            if "=" in line and not line.lstrip().startswith("#"):
+                key, val = line.split("=", 1)
+                vals[key.strip()] = val.strip()
+        if vals.get("kernel_source_sha256") != src:
+            return None
+        return float(vals["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        top = sorted(sm)[len(sm) // 2:]
+        return {"sm_mhz": statistics.median(top), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------------------------------ reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle as O
+    from paper_1602_06621_gb300 import inputs as I
+
+    A = O.OracleCSR.from_any(I.workload_large(args.scale))
+    d = O.default_params(A.m, A.n)
+    frac = 0.05
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(A.m, max(1, int(frac * A.m)), replace=False))
+    cols = np.sort(rng.choice(A.n, max(1, int(frac * A.n)), replace=False))
+    z = (np.zeros(A.m), np.zeros(A.n), np.zeros(A.m), np.zeros(A.n))
+
+    def one(t):
+        O.psgd_step_sampled(A, *z, rows, cols, t, k=args.k, seed=0, **d)
+
+    for t in range(1, args.warmup + 1):
+        one(t)
+    t0 = time.perf_counter()
+    for t in range(1, args.steps + 1):
+        one(t)
+    el = time.perf_counter() - t0
+    # Each step is 5% of the rows' and 5% of the columns' work of one iteration: frac * k full-matrix probe pairs.
+    value = frac * args.k * args.steps / el
+    sample = (f"one iteration of Algorithm 1 (k={args.k}) evaluated at a fixed random 5% of the rows and 5% of "
+              f"the columns of the full matrix per step, single-threaded FP64 C oracle; value in full-matrix "
+              f"probe pairs per second")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(A, args.k, args.T), "m": A.m, "n": A.n, "nnz": A.nnz,
+                   "k": args.k, "T": args.T},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------ our arm
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    from paper_1602_06621_gb300 import inputs as I
+    from paper_1602_06621_gb300 import sme
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    k, T = args.k, args.T
+    A = I.workload_large(args.scale, seed=2 + rank)
+    m, n, nnz = A.m, A.n, A.nnz
+    op = sme.sme_op_create_csr(m, n, A.row_ptr, A.col_idx, A.vals)
+    f32 = dict(dtype=torch.float32, device="cuda")
+    u, v, ub, vb = (torch.zeros(m, **f32), torch.zeros(n, **f32), torch.zeros(m, **f32), torch.zeros(n, **f32))
+    xstar = torch.tensor(I.normal_vector(n, 100 + rank, np.float32), device="cuda")
+    # b = A x* computed by the library's own FP64-accumulating product is not exposed; use torch sparse on
+    # the host copy for the right-hand side (input preparation, outside any timed region).
+    import scipy.sparse as sps
+    S = sps.csr_matrix((A.vals.astype(np.float64), A.col_idx, A.row_ptr), shape=(m, n))
+    b = torch.tensor((S @ xstar.cpu().double().numpy()).astype(np.float32), device="cuda")
+    x = torch.zeros(n, **f32)
+    do_lsqr = not args.no_lsqr
+
+    def step():
+        u.zero_(), v.zero_(), ub.zero_(), vb.zero_()
+        sme.sme_equilibrate(op, u, v, ub, vb, T=T, k=k, seed=0, flags=sme.SME_EQ_TIMED | sme.SME_EQ_ASYNC)
+        res = None
+        if do_lsqr:
+            res = sme.sme_lsqr(op, ub, vb, b, x, tol=1e-6, max_iters=20000, check_every=10)
+        return res
+
+    for _ in range(args.warmup):
+        step()
+    sme.sme_op_check(op)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    loop_ms = []
+    lsqr_res = []
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            r = step()
+            loop_ms.append(sme.sme_op_get_info(op)["last_loop_ms"])
+            if r is not None:
+                lsqr_res.append(r)
+        ev1.record(stream)
+        barrier()
+    sme.sme_op_check(op)
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if dist is not None:
+        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    clocks = clk.summary()
+
+    units_per_step = k * T
+    value = world * units_per_step * args.steps / elapsed
+    iter_s = (sum(loop_ms) / len(loop_ms)) / 1e3 / T
+    bytes_iter = algorithmic_bytes_per_iteration(m, n, nnz)
+    peak, peak_kind = measured_hbm_peak()
+    achieved = bytes_iter / iter_s / 1e9
+    launches_per_step = T + 4 + (lsqr_res[0]["gpu_launches"] if lsqr_res and "gpu_launches" in lsqr_res[0] else 0)
+
+    # Quality of the last step's scaling (outside the timed region).
+    quality = sme.sme_evaluate(op, ub, vb)
+
+    e2e = None
+    if not args.no_e2e:
+        # Through the public API from pinned host buffers: create the operator (H2D copy + device build),
+        # equilibrate, solve, read D, E and x back.
+        rp_h = torch.from_numpy(A.row_ptr).pin_memory()
+        ci_h = torch.from_numpy(A.col_idx).pin_memory()
+        va_h = torch.from_numpy(A.vals).pin_memory()
+        out_h = torch.empty(m + 2 * n, dtype=torch.float32).pin_memory()
+        e2e_steps = max(1, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            op2 = sme.sme_op_create_csr(m, n, rp_h.numpy(), ci_h.numpy(), va_h.numpy())
+            u2, v2, ub2, vb2 = (torch.zeros(m, **f32), torch.zeros(n, **f32), torch.zeros(m, **f32),
+                                torch.zeros(n, **f32))
+            sme.sme_equilibrate(op2, u2, v2, ub2, vb2, T=T, k=k, seed=0)
+            x2 = torch.zeros(n, **f32)
+            if do_lsqr:
+                sme.sme_lsqr(op2, ub2, vb2, b, x2, tol=1e-6, max_iters=20000, check_every=10)
+            out_h[:m].copy_(ub2, non_blocking=True)
+            out_h[m:m + n].copy_(vb2, non_blocking=True)
+            out_h[m + n:].copy_(x2, non_blocking=True)
+            torch.cuda.synchronize()
+            sme.sme_op_destroy(op2)
+        barrier()
+        e2e_el = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([e2e_el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_el = float(t.item())
+        h2d = 4 * (m + 1) + 8 * nnz + 4 * m  # CSR arrays + b
+        e2e = {"value": world * units_per_step * e2e_steps / e2e_el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 4 * (m + 2 * n), "steps": e2e_steps, "ms_per_step": 1e3 * e2e_el / e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        A64 = O.OracleCSR.from_any(A)
+        t0 = time.perf_counter()
+        O.equilibrate(A64, T=1, k=k, seed=0)
+        el = time.perf_counter() - t0
+        cpu = {"value": k / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"1 iteration of Algorithm 1 (k={k}) on the full matrix, single-threaded FP64 C oracle "
+                         f"({el:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(A, k, T), "m": m, "n": n, "nnz": nnz, "k": k, "T": T,
+                       "l2": "inputs larger than L2: each pass streams a 160 MB copy of A (129 MB L2)",
+                       "parallelism": "independent matrix per GPU" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": recorded_traffic(), "peak_kind": peak_kind,
+                         "kernel": "sgd_iteration<float,32> (one iteration of Algorithm 1, both passes)",
+                         "algorithmic_bytes_per_launch": bytes_iter, "launch_us": iter_s * 1e6},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+            "equilibration": {"iteration_us": iter_s * 1e6, "probe_pairs_per_s_loop": k / iter_s,
+                              "hbm_gbs": achieved, "row_spread": quality["row_spread"],
+                              "col_spread": quality["col_spread"], "rms": quality["rms"],
+                              "objective": quality["objective"]},
+        }
+        if lsqr_res:
+            last = lsqr_res[-1]
+            line["lsqr"] = {k2: last[k2] for k2 in ("iters", "rel_residual", "converged")}
+        print(json.dumps(line), flush=True)
+    sme.sme_op_destroy(op)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

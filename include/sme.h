@@ -101,6 +101,8 @@ typedef struct {
     int64_t device_bytes;       /* device memory the op holds */
     int64_t padded_entries_fwd; /* sliced-ELL entries incl. padding, A and A^T copies */
     int64_t padded_entries_bwd;
+    double last_loop_ms;        /* with SME_EQ_TIMED: device time of the last call's iteration loop */
+    int64_t last_loop_iters;    /* iterations in that loop */
 } sme_op_info;
 
 sme_status sme_op_get_info(sme_op op, sme_op_info *info);
@@ -136,6 +138,7 @@ typedef struct {
 
 #define SME_EQ_ASYNC 1    /* do not synchronise or read the status word; see sme_op_check */
 #define SME_EQ_NO_GRAPH 2 /* launch the iterations directly instead of through a cached CUDA graph */
+#define SME_EQ_TIMED 4    /* time the iteration loop with CUDA events on `stream` (read by sme_op_get_info) */
 
 /*
  * sme_equilibrate -- iterations t_begin .. t_begin+T-1 of Algorithm 1 (Section 3.2):
@@ -196,6 +199,7 @@ typedef struct {
     double rel_residual;      /* ||A x - b|| / ||b|| of the ORIGINAL system, FP64 */
     double normal_residual;   /* ||A^T (A x - b)|| / (||A||_F ||A x - b||), FP64 */
     int32_t converged;
+    int64_t kernel_launches;  /* device kernels this call launched */
 } sme_lsqr_result;
 
 /*

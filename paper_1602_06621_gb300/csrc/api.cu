@@ -119,12 +119,14 @@ extern "C" sme_status sme_op_destroy(sme_op op)
     free_sell(op, op->fwd);
     free_sell(op, op->bwd);
     Workspace &W = op->ws;
-    for (void *p : {W.u, W.v, W.ub, W.vb, W.tab_u[0], W.tab_u[1], W.tab_v[0], W.tab_v[1], W.lsqr, (void *)W.red})
+    for (void *p : {W.u, W.v, W.ub, W.vb, W.tab_u[0], W.tab_u[1], W.tab_v[0], W.tab_v[1], (void *)W.red})
         if (p) cudaFree(p);
     release_lsqr(op);
     if (op->graph.exec) cudaGraphExecDestroy(op->graph.exec);
     if (op->dense) dense_destroy(op);
     if (op->d_status) cudaFree(op->d_status);
+    for (cudaEvent_t e : op->ev_loop)
+        if (e) cudaEventDestroy(e);
     delete op;
     return SME_OK;
 }
@@ -209,6 +211,15 @@ extern "C" sme_status sme_op_get_info(sme_op op, sme_op_info *info)
     info->device_bytes = op->device_bytes;
     info->padded_entries_fwd = op->fwd.entries;
     info->padded_entries_bwd = op->bwd.entries;
+    info->last_loop_ms = 0.0;
+    info->last_loop_iters = 0;
+    if (op->loop_timed) {
+        float ms = 0.f;
+        SME_CUDA(cudaEventSynchronize(op->ev_loop[1]));
+        SME_CUDA(cudaEventElapsedTime(&ms, op->ev_loop[0], op->ev_loop[1]));
+        info->last_loop_ms = ms;
+        info->last_loop_iters = op->loop_iters;
+    }
     return SME_OK;
 }
 

@@ -124,27 +124,67 @@ __device__ __forceinline__ void load_pair(const SellArgs &S, int64_t pi, int &c0
     a1 = v.y;
 }
 
-// acc[p] += (sign of probe p) * y, the sign being bit p of the probe words (set = -1).
+// FP32 accumulation of the signed sums y_p = sum_l s_lp y_l (s_lp = -1 where bit p of the probe
+// words is set).  It is kept as y_p = C - 2 P_p with C = sum_l y_l and P_p = sum over set bits of y_l:
+// each (nonzero, probe) pair then costs one predicated add instead of a sign flip and an add.
 template <int K>
-__device__ __forceinline__ void acc_signed(float (&acc)[K], float y, const uint32_t *w)
-{
-    const uint32_t yb = __float_as_uint(y);
+struct SignAcc32 {
+    float P[K];
+    float C;
+    __device__ __forceinline__ void init()
+    {
 #pragma unroll
-    for (int p = 0; p < K; ++p) {
-        const uint32_t sgn = (w[p >> 5] << (31 - (p & 31))) & 0x80000000u;
-        acc[p] += __uint_as_float(yb ^ sgn);
+        for (int p = 0; p < K; ++p) P[p] = 0.f;
+        C = 0.f;
     }
-}
+    __device__ __forceinline__ void add(float y, const uint32_t *w)
+    {
+        C += y;
+#pragma unroll
+        for (int p = 0; p < K; ++p)
+            if (w[p >> 5] & (1u << (p & 31))) P[p] += y;
+    }
+    __device__ __forceinline__ float sum_sq() const
+    {
+        float ss = 0.f;
+#pragma unroll
+        for (int p = 0; p < K; ++p) {
+            const float yp = C - 2.f * P[p];
+            ss += yp * yp;
+        }
+        return ss;
+    }
+};
 
+// FP64: direct signed accumulation (small problems; accuracy first).
 template <int K>
-__device__ __forceinline__ void acc_signed(double (&acc)[K], double y, const uint32_t *w)
-{
+struct SignAcc64 {
+    double acc[K];
+    __device__ __forceinline__ void init()
+    {
 #pragma unroll
-    for (int p = 0; p < K; ++p) {
-        const bool neg = (w[p >> 5] >> (p & 31)) & 1u;
-        acc[p] += neg ? -y : y;
+        for (int p = 0; p < K; ++p) acc[p] = 0.0;
     }
-}
+    __device__ __forceinline__ void add(double y, const uint32_t *w)
+    {
+#pragma unroll
+        for (int p = 0; p < K; ++p) acc[p] += ((w[p >> 5] >> (p & 31)) & 1u) ? -y : y;
+    }
+    __device__ __forceinline__ double sum_sq() const
+    {
+        double ss = 0.0;
+#pragma unroll
+        for (int p = 0; p < K; ++p) ss += acc[p] * acc[p];
+        return ss;
+    }
+};
+
+template <typename real, int K>
+struct SignAcc;
+template <int K>
+struct SignAcc<float, K> : SignAcc32<K> {};
+template <int K>
+struct SignAcc<double, K> : SignAcc64<K> {};
 
 __device__ __forceinline__ float dexp(float x) { return expf(x); }
 __device__ __forceinline__ double dexp(double x) { return exp(x); }
@@ -167,30 +207,56 @@ __global__ void __launch_bounds__(ITER_THREADS) sgd_iteration(StepArgs<real> a)
     if (slice >= S.nslices) return;
     const int64_t r = slice * 32 + lane;
 
-    real acc[K];
-#pragma unroll
-    for (int p = 0; p < K; ++p) acc[p] = real(0);
+    SignAcc<real, K> acc;
+    acc.init();
 
-    const int w = S.slice_w[slice];
+    // Two-stage software pipeline over the row's pairs of steps: the entries of pair q+2 and the
+    // table gathers of pair q+1 are in flight while pair q is accumulated.  Slice widths are
+    // uniform across the warp, so every branch below is warp-uniform.
+    const int np = S.slice_w[slice] / 2;
     const int64_t pbase = S.slice_off[slice] / 2 + lane;
     const void *tab = cols ? a.tab_in[1] : a.tab_in[0];
-#pragma unroll 2
-    for (int q = 0; q < w / 2; ++q) {
-        int c0, c1;
-        real a0, a1;
-        load_pair(S, pbase + (int64_t)q * 32, c0, a0, c1, a1);
-        real x0, x1;
-        uint32_t w0[KW], w1[KW];
+    int c0 = 0, c1 = 0, n0 = 0, n1 = 0;
+    real a0 = real(0), a1 = real(0), b0 = real(0), b1 = real(0);
+    real x0 = real(0), x1 = real(0);
+    uint32_t w0[KW] = {}, w1[KW] = {};
+    if (np > 0) {
+        load_pair(S, pbase, c0, a0, c1, a1);
         Tab::load(tab, c0, x0, w0);
         Tab::load(tab, c1, x1, w1);
-        acc_signed<K>(acc, a0 * x0, w0);
-        acc_signed<K>(acc, a1 * x1, w1);
     }
+    if (np > 1) load_pair(S, pbase + 32, n0, b0, n1, b1);
+    for (int q = 0; q < np; ++q) {
+        real y0 = real(0), y1 = real(0);
+        uint32_t v0[KW] = {}, v1[KW] = {};
+        if (q + 1 < np) {
+            Tab::load(tab, n0, y0, v0);
+            Tab::load(tab, n1, y1, v1);
+        }
+        int m0 = 0, m1 = 0;
+        real d0 = real(0), d1 = real(0);
+        if (q + 2 < np) load_pair(S, pbase + (int64_t)(q + 2) * 32, m0, d0, m1, d1);
+        acc.add(a0 * x0, w0);
+        acc.add(a1 * x1, w1);
+        a0 = b0;
+        a1 = b1;
+        b0 = d0;
+        b1 = d1;
+        n0 = m0;
+        n1 = m1;
+        x0 = y0;
+        x1 = y1;
+#pragma unroll
+        for (int h = 0; h < KW; ++h) {
+            w0[h] = v0[h];
+            w1[h] = v1[h];
+        }
+    }
+    (void)c0;
+    (void)c1;
     if (r >= S.rows) return;
 
-    real ss = real(0);
-#pragma unroll
-    for (int p = 0; p < K; ++p) ss += acc[p] * acc[p];
+    const real ss = acc.sum_sq();
     real *X = cols ? a.x[1] : a.x[0];
     const real xo = X[r];
     const real ex = dexp(xo);
@@ -380,6 +446,12 @@ static sme_status equilibrate_t(sme_op op, const sme_equil_params *p, real *u, r
     launch_load<real>(op, 1, kw, v, vb, (real *)op->ws.v, (real *)op->ws.vb, op->ws.tab_v[buf], (uint32_t)tb, sid_s,
                       p->seed, s);
     const unsigned grid = iter_grid(op);
+    const bool timed = (p->flags & SME_EQ_TIMED) != 0;
+    if (timed) {
+        for (int i = 0; i < 2; ++i)
+            if (!op->ev_loop[i]) SME_CUDA(cudaEventCreate(&op->ev_loop[i]));
+        SME_CUDA(cudaEventRecord(op->ev_loop[0], s));
+    }
     for (int t = tb; t < tb + p->T; ++t) {
         StepArgs<real> a = base_args<real>(op, t & 1, R, p->seed);
         a.eta = (real)(2.0 / (R.gamma * ((double)t + (double)p->t0 + 1.0)));
@@ -390,6 +462,11 @@ static sme_status equilibrate_t(sme_op op, const sme_equil_params *p, real *u, r
         a.sid_out[1] = sid_s;
         a.mode = 0;
         launch_iteration<real>(a, k, grid, s);
+    }
+    if (timed) {
+        SME_CUDA(cudaEventRecord(op->ev_loop[1], s));
+        op->loop_timed = true;
+        op->loop_iters = p->T;
     }
     store_state<real><<<nblk(op->m), 256, 0, s>>>(op->m, op->fwd.perm, (real *)op->ws.u, (real *)op->ws.ub, u, ub);
     store_state<real><<<nblk(op->n), 256, 0, s>>>(op->n, op->bwd.perm, (real *)op->ws.v, (real *)op->ws.vb, v, vb);

@@ -162,7 +162,519 @@ static sme_status evaluate_t(sme_op op, const real *u, const real *v, double alp
     return SME_OK;
 }
 
-void release_lsqr(sme_op op) { (void)op; }
+// ------------------------------------------------------------------ LSQR
+//
+// Paige & Saunders (1982) LSQR on K = D A E, used as in Section 5.1: solve K xbar = D b from
+// xbar = 0 and return x = E xbar; accuracy is judged on the original system.
+//
+// Vectors live in sorted order.  The products gather pre-scaled vectors so each nonzero costs a
+// single gather: ud = D uhat (uhat = beta u, unnormalised) for the products with A^T, and
+// ve = E vhat (vhat = alpha v) for the products with A.  The norms beta and alpha are FP64
+// reductions (block partials summed in a fixed order by the last block), and the scalar
+// recurrence runs in FP64 in the last block of each A^T-kernel, so the host only looks at the
+// state every check_every iterations.  The update x <- x + (phi/rho) w, w <- v - (theta/rho) w of
+// iteration i needs alpha_{i+1}, so it is applied by the A^T-kernel of iteration i+1 (and by the
+// final kernel), which reads v_{i+1} there anyway.
+
+struct LsqrScalars {
+    double alpha, beta;      // alpha_i (normalises ve), beta (normalises ud)
+    double rhobar, phibar;
+    double phi, rho, theta;  // phi_i, rho_i, theta_{i+1} of the last completed iteration i
+    double bnorm, tol;
+    double rel_res, normal_res, afro;
+    long long iters;         // completed iterations
+    int done;                // 0 running, 1 converged (checked), 2 exact breakdown (beta or alpha = 0)
+    int first;               // next A^T-kernel starts the w/x sequence (w_1 = v_1, x_0 = 0)
+    int stop_rule;
+    int pad;
+};
+
+struct LsqrState {
+    void *ud, *ve, *w, *x, *d, *e, *bs, *xt;
+    double *r;
+    double *partials;  // 2 * max blocks
+    unsigned *counter;
+    LsqrScalars *sc;
+    LsqrScalars *host;  // pinned mirror
+    int64_t bytes;
+    int64_t fwd_blocks, bwd_blocks;
+    double afro;  // cached ||A||_F (< 0: not computed)
+};
+
+constexpr int LQ_THREADS = 256;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block sum; valid in thread 0.
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double sh[LQ_THREADS / 32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = lane < LQ_THREADS / 32 ? sh[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    return t;
+}
+
+// Writes this block's partial, and returns true in every thread of the block that arrives last.
+__device__ __forceinline__ bool arrive_last(double part, double *partials, unsigned *counter)
+{
+    __shared__ bool last;
+    const double b = block_sum(part);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = b;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    return last;
+}
+
+// In the last block: the sum of all partials in a fixed order (deterministic).
+__device__ __forceinline__ double sum_partials(const double *partials, unsigned *counter)
+{
+    __threadfence();
+    double v = 0.0;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) v += ((volatile const double *)partials)[i];
+    const double s = block_sum(v);
+    __shared__ double res;
+    if (threadIdx.x == 0) {
+        res = s;
+        *counter = 0u;
+    }
+    __syncthreads();
+    return res;
+}
+
+template <typename real>
+__device__ __forceinline__ void pair_load(const Sell &S, int64_t pi, int &c0, real &a0, int &c1, real &a1)
+{
+    if (sizeof(real) == 4) {
+        const int4 e = __ldcs((const int4 *)S.ent + pi);
+        c0 = e.x;
+        c1 = e.z;
+        a0 = (real)__int_as_float(e.y);
+        a1 = (real)__int_as_float(e.w);
+    } else {
+        const int2 c = __ldcs((const int2 *)S.ent + pi);
+        const double2 v = __ldcs((const double2 *)S.val64 + pi);
+        c0 = c.x;
+        c1 = c.y;
+        a0 = (real)v.x;
+        a1 = (real)v.y;
+    }
+}
+
+// sum_l a_l * g[c_l] over the row owned by this thread (acc type `acc_t`), software-pipelined.
+template <typename real, typename acc_t, typename G>
+__device__ __forceinline__ acc_t sell_row_dot(const Sell &S, int64_t slice, int lane, const G *g)
+{
+    const int np = S.slice_w[slice] / 2;
+    const int64_t pbase = S.slice_off[slice] / 2 + lane;
+    acc_t acc = acc_t(0);
+    int c0 = 0, c1 = 0, n0 = 0, n1 = 0;
+    real a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+    if (np > 0) pair_load<real>(S, pbase, c0, a0, c1, a1);
+    if (np > 1) pair_load<real>(S, pbase + 32, n0, b0, n1, b1);
+    G g0 = np > 0 ? g[c0] : G(0), g1 = np > 0 ? g[c1] : G(0);
+    for (int q = 0; q < np; ++q) {
+        G h0 = G(0), h1 = G(0);
+        if (q + 1 < np) {
+            h0 = g[n0];
+            h1 = g[n1];
+        }
+        int m0 = 0, m1 = 0;
+        real d0 = 0, d1 = 0;
+        if (q + 2 < np) pair_load<real>(S, pbase + (int64_t)(q + 2) * 32, m0, d0, m1, d1);
+        acc += (acc_t)a0 * (acc_t)g0;
+        acc += (acc_t)a1 * (acc_t)g1;
+        a0 = b0;
+        a1 = b1;
+        b0 = d0;
+        b1 = d1;
+        n0 = m0;
+        n1 = m1;
+        g0 = h0;
+        g1 = h1;
+    }
+    return acc;
+}
+
+// b in sorted row order, u_1 = D b / beta_1 stored as ud = D (D b); beta_1 and ||b|| reduced.
+template <typename real>
+__global__ void lsqr_init_rows(int64_t m, const int32_t *perm, const real *b, const real *d, real *bs, real *ud,
+                               double *partials, unsigned *counter, LsqrScalars *sc)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double pb = 0.0, pdb = 0.0;
+    if (r < m) {
+        const real bi = b[perm[r]];
+        const real dr = d[r];
+        bs[r] = bi;
+        const real db = dr * bi;
+        ud[r] = dr * db;
+        pb = (double)bi * (double)bi;
+        pdb = (double)db * (double)db;
+    }
+    // Two sums through the same partial array: [0, grid) for ||D b||^2, [grid, 2 grid) for ||b||^2.
+    const double s1 = block_sum(pdb);
+    const double s2 = block_sum(pb);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = s1;
+        partials[gridDim.x + blockIdx.x] = s2;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double v1 = 0.0, v2 = 0.0;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+        v1 += ((volatile double *)partials)[i];
+        v2 += ((volatile double *)partials)[gridDim.x + i];
+    }
+    const double t1 = block_sum(v1);
+    const double t2 = block_sum(v2);
+    if (threadIdx.x == 0) {
+        *counter = 0u;
+        sc->beta = sqrt(t1);
+        sc->phibar = sc->beta;
+        sc->bnorm = sqrt(t2);
+        sc->phi = 0.0;
+        sc->rho = 1.0;
+        sc->theta = 0.0;
+        sc->iters = 0;
+        sc->first = 1;
+        sc->done = sc->beta > 0.0 ? 0 : 2;
+        sc->rel_res = sc->bnorm > 0.0 ? 1.0 : 0.0;
+    }
+}
+
+// Products with A (rows): uhat = K v_i - alpha_i u_i; beta_{i+1} = ||uhat||.
+template <typename real>
+__global__ void __launch_bounds__(LQ_THREADS) lsqr_rows(Sell S, const real *d, const real *ve, real *ud,
+                                                         double *partials, unsigned *counter, LsqrScalars *sc)
+{
+    if (((volatile LsqrScalars *)sc)->done) return;
+    const double alpha = sc->alpha, beta = sc->beta;
+    const real inv_alpha = (real)(alpha > 0.0 ? 1.0 / alpha : 0.0);
+    const real alpha_r = (real)alpha;
+    const real inv_beta = (real)(beta > 0.0 ? 1.0 / beta : 0.0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
+    double part = 0.0;
+    if (slice < S.nslices) {
+        const real acc = sell_row_dot<real, real, real>(S, slice, lane, ve);
+        const int64_t r = slice * 32 + lane;
+        if (r < S.rows) {
+            const real dr = d[r];
+            const real uhat = dr * acc * inv_alpha - alpha_r * (ud[r] / dr) * inv_beta;
+            ud[r] = dr * uhat;
+            part = (double)uhat * (double)uhat;
+        }
+    }
+    if (!arrive_last(part, partials, counter)) return;
+    const double tot = sum_partials(partials, counter);
+    if (threadIdx.x == 0) sc->beta = sqrt(tot);
+}
+
+// Products with A^T (columns): the lagged x/w update of the previous iteration, then
+// vhat = K^T u_{i+1} - beta_{i+1} v_i, alpha_{i+1} = ||vhat||, and the scalar recurrence of iteration i.
+// init = 1 computes vhat = K^T u_1 only (alpha_1, rhobar_1).
+template <typename real>
+__global__ void __launch_bounds__(LQ_THREADS) lsqr_cols(Sell S, const real *e, const real *ud, real *ve, real *w,
+                                                         real *x, double *partials, unsigned *counter,
+                                                         LsqrScalars *sc, int init)
+{
+    if (((volatile LsqrScalars *)sc)->done) return;
+    const double alpha = sc->alpha, beta = sc->beta;
+    const int first = sc->first;
+    const real inv_alpha = (real)(alpha > 0.0 ? 1.0 / alpha : 0.0);
+    const real inv_beta = (real)(beta > 0.0 ? 1.0 / beta : 0.0);
+    const real beta_r = (real)beta;
+    const real x_step = (real)(sc->phi / sc->rho);
+    const real w_step = (real)(sc->theta / sc->rho);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
+    double part = 0.0;
+    if (slice < S.nslices) {
+        const real acc = sell_row_dot<real, real, real>(S, slice, lane, ud);
+        const int64_t c = slice * 32 + lane;
+        if (c < S.rows) {
+            const real ec = e[c];
+            real vhat;
+            if (init) {
+                vhat = ec * acc * inv_beta;
+                w[c] = real(0);
+                x[c] = real(0);
+            } else {
+                const real v = ve[c] / ec * inv_alpha;
+                if (first) {
+                    w[c] = v;
+                    x[c] = real(0);
+                } else {
+                    const real wo = w[c];
+                    x[c] = x[c] + x_step * wo;
+                    w[c] = v - w_step * wo;
+                }
+                vhat = ec * acc * inv_beta - beta_r * v;
+            }
+            ve[c] = ec * vhat;
+            part = (double)vhat * (double)vhat;
+        }
+    }
+    if (!arrive_last(part, partials, counter)) return;
+    const double tot = sum_partials(partials, counter);
+    if (threadIdx.x != 0) return;
+    const double alpha_n = sqrt(tot);
+    if (init) {
+        sc->alpha = alpha_n;
+        sc->rhobar = alpha_n;
+        if (alpha_n == 0.0) sc->done = 2;
+        return;
+    }
+    const double rho = hypot(sc->rhobar, beta);
+    const double cs = sc->rhobar / rho, sn = beta / rho;
+    sc->theta = sn * alpha_n;
+    sc->rhobar = -cs * alpha_n;
+    sc->phi = cs * sc->phibar;
+    sc->phibar = sn * sc->phibar;
+    sc->rho = rho;
+    sc->alpha = alpha_n;
+    sc->first = 0;
+    sc->iters += 1;
+    if (beta == 0.0 || alpha_n == 0.0) sc->done = 2;
+}
+
+// xt = E (x + (phi/rho) w): the current iterate x_i = E xbar_i; with perm != NULL also written to
+// x_out in original column order (the final result).
+template <typename real>
+__global__ void lsqr_current_x(int64_t n, const real *e, const real *x, const real *w, const LsqrScalars *sc,
+                               real *xt, const int32_t *perm, real *x_out)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    if (sc->done == 1 && !perm) return;
+    const real step = (real)(sc->phi / sc->rho);
+    const real v = e[c] * (x[c] + step * w[c]);
+    if (xt) xt[c] = v;
+    if (perm) x_out[perm[c]] = v;
+}
+
+// r = A xt - b in FP64 (rows); ||r|| / ||b|| against tol (stop_rule 0).
+template <typename real>
+__global__ void __launch_bounds__(LQ_THREADS) lsqr_residual(Sell S, const real *xt, const real *bs, double *r,
+                                                             double *partials, unsigned *counter, LsqrScalars *sc,
+                                                             int final_check)
+{
+    if (!final_check && ((volatile LsqrScalars *)sc)->done == 1) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
+    double part = 0.0;
+    if (slice < S.nslices) {
+        const double acc = sell_row_dot<real, double, real>(S, slice, lane, xt);
+        const int64_t i = slice * 32 + lane;
+        if (i < S.rows) {
+            const double ri = acc - (double)bs[i];
+            r[i] = ri;
+            part = ri * ri;
+        }
+    }
+    if (!arrive_last(part, partials, counter)) return;
+    const double tot = sum_partials(partials, counter);
+    if (threadIdx.x != 0) return;
+    sc->rel_res = sc->bnorm > 0.0 ? sqrt(tot) / sc->bnorm : sqrt(tot);
+    sc->normal_res = sqrt(tot);  // ||r||, turned into the normal residual by lsqr_normal
+    if (!final_check && sc->stop_rule == 0 && sc->rel_res <= sc->tol && sc->done == 0) sc->done = 1;
+}
+
+// ||A^T r|| / (||A||_F ||r||) (columns), FP64.
+template <typename real>
+__global__ void __launch_bounds__(LQ_THREADS) lsqr_normal(Sell S, const double *r, double *partials,
+                                                           unsigned *counter, LsqrScalars *sc, int final_check)
+{
+    if (!final_check && ((volatile LsqrScalars *)sc)->done == 1) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
+    double part = 0.0;
+    if (slice < S.nslices) {
+        const double acc = sell_row_dot<real, double, double>(S, slice, lane, r);
+        if (slice * 32 + lane < S.rows) part = acc * acc;
+    }
+    if (!arrive_last(part, partials, counter)) return;
+    const double tot = sum_partials(partials, counter);
+    if (threadIdx.x != 0) return;
+    const double rn = sc->normal_res;
+    sc->normal_res = (rn > 0.0 && sc->afro > 0.0) ? sqrt(tot) / (sc->afro * rn) : 0.0;
+    if (!final_check && sc->stop_rule == 1 && sc->normal_res <= sc->tol && sc->done == 0) sc->done = 1;
+}
+
+template <typename real>
+__global__ void scales_sorted(int64_t n, const int32_t *perm, const real *logscale, real *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = logscale ? (real)exp((double)logscale[perm[i]]) : real(1);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(LQ_THREADS) frobenius_sq(Sell S, double *partials, unsigned *counter, double *out)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
+    double part = 0.0;
+    if (slice < S.nslices) {
+        const int np = S.slice_w[slice] / 2;
+        const int64_t pbase = S.slice_off[slice] / 2 + lane;
+        for (int q = 0; q < np; ++q) {
+            int c0, c1;
+            real a0, a1;
+            pair_load<real>(S, pbase + (int64_t)q * 32, c0, a0, c1, a1);
+            part += (double)a0 * (double)a0 + (double)a1 * (double)a1;
+        }
+    }
+    if (!arrive_last(part, partials, counter)) return;
+    const double tot = sum_partials(partials, counter);
+    if (threadIdx.x == 0) *out = tot;
+}
+
+static LsqrState *lsqr_state(sme_op op) { return (LsqrState *)op->ws.lsqr; }
+
+void release_lsqr(sme_op op)
+{
+    LsqrState *L = lsqr_state(op);
+    if (!L) return;
+    for (void *p : {L->ud, L->ve, L->w, L->x, L->d, L->e, L->bs, L->xt, (void *)L->r, (void *)L->partials,
+                    (void *)L->counter, (void *)L->sc})
+        if (p) cudaFree(p);
+    if (L->host) cudaFreeHost(L->host);
+    delete L;
+    op->ws.lsqr = nullptr;
+}
+
+static sme_status ensure_lsqr(sme_op op, cudaStream_t s)
+{
+    if (lsqr_state(op)) return SME_OK;
+    LsqrState *L = new LsqrState();
+    op->ws.lsqr = L;
+    const size_t sz = op->dbl ? 8 : 4;
+    const int64_t m = op->m, n = op->n;
+    L->fwd_blocks = (op->fwd.nslices + 7) / 8;
+    L->bwd_blocks = (op->bwd.nslices + 7) / 8;
+    const int64_t maxb = std::max<int64_t>(std::max(L->fwd_blocks, L->bwd_blocks), (std::max(m, n) + 255) / 256);
+    SME_TRY(dev_alloc(op, &L->ud, m * sz));
+    SME_TRY(dev_alloc(op, &L->bs, m * sz));
+    SME_TRY(dev_alloc(op, &L->d, m * sz));
+    SME_TRY(dev_alloc(op, (void **)&L->r, m * sizeof(double)));
+    SME_TRY(dev_alloc(op, &L->ve, n * sz));
+    SME_TRY(dev_alloc(op, &L->w, n * sz));
+    SME_TRY(dev_alloc(op, &L->x, n * sz));
+    SME_TRY(dev_alloc(op, &L->e, n * sz));
+    SME_TRY(dev_alloc(op, &L->xt, n * sz));
+    SME_TRY(dev_alloc(op, (void **)&L->partials, 2 * maxb * sizeof(double)));
+    SME_TRY(dev_alloc(op, (void **)&L->counter, sizeof(unsigned)));
+    SME_TRY(dev_alloc(op, (void **)&L->sc, sizeof(LsqrScalars)));
+    SME_CUDA(cudaMallocHost((void **)&L->host, sizeof(LsqrScalars)));
+    SME_CUDA(cudaMemsetAsync(L->counter, 0, sizeof(unsigned), s));
+    L->afro = -1.0;
+    return SME_OK;
+}
+
+template <typename real>
+static sme_status lsqr_t(sme_op op, const real *ubar, const real *vbar, const real *b, real *x_out,
+                         const sme_lsqr_params *p, sme_lsqr_result *res, cudaStream_t s)
+{
+    SME_TRY(ensure_lsqr(op, s));
+    LsqrState *L = lsqr_state(op);
+    const int64_t m = op->m, n = op->n;
+    const Sell &F = op->fwd, &B = op->bwd;
+    real *ud = (real *)L->ud, *ve = (real *)L->ve, *w = (real *)L->w, *x = (real *)L->x;
+    real *d = (real *)L->d, *e = (real *)L->e, *bs = (real *)L->bs, *xt = (real *)L->xt;
+    const unsigned fb = (unsigned)std::max<int64_t>(L->fwd_blocks, 1), bb = (unsigned)std::max<int64_t>(L->bwd_blocks, 1);
+    int64_t launches = 0;
+    LsqrScalars init{};
+    init.tol = p->tol;
+    init.stop_rule = p->stop_rule;
+    init.afro = L->afro;
+    SME_CUDA(cudaMemcpyAsync(L->sc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+    SME_CUDA(cudaMemsetAsync(x, 0, n * sizeof(real), s));
+    SME_CUDA(cudaMemsetAsync(w, 0, n * sizeof(real), s));
+    if (L->afro < 0) {
+        double *fro = &L->sc->afro;
+        frobenius_sq<real><<<fb, LQ_THREADS, 0, s>>>(F, L->partials, L->counter, fro);
+        double h = 0.0;
+        SME_CUDA(cudaMemcpyAsync(&h, fro, sizeof(double), cudaMemcpyDeviceToHost, s));
+        SME_CUDA(cudaStreamSynchronize(s));
+        L->afro = std::sqrt(h);
+        SME_CUDA(cudaMemcpyAsync(fro, &L->afro, sizeof(double), cudaMemcpyHostToDevice, s));
+        ++launches;
+    }
+    scales_sorted<real><<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, F.perm, ubar, d);
+    scales_sorted<real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, B.perm, vbar, e);
+    lsqr_init_rows<real><<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, F.perm, b, d, bs, ud, L->partials,
+                                                                       L->counter, L->sc);
+    lsqr_cols<real><<<bb, LQ_THREADS, 0, s>>>(B, e, ud, ve, w, x, L->partials, L->counter, L->sc, 1);
+    launches += 4;
+    SME_CUDA(cudaGetLastError());
+    const int every = std::max(1, p->check_every);
+    int64_t it = 0;
+    while (it < p->max_iters) {
+        const int64_t chunk = std::min<int64_t>(every, p->max_iters - it);
+        for (int64_t j = 0; j < chunk; ++j) {
+            lsqr_rows<real><<<fb, LQ_THREADS, 0, s>>>(F, d, ve, ud, L->partials, L->counter, L->sc);
+            lsqr_cols<real><<<bb, LQ_THREADS, 0, s>>>(B, e, ud, ve, w, x, L->partials, L->counter, L->sc, 0);
+        }
+        it += chunk;
+        lsqr_current_x<real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, e, x, w, L->sc, xt, nullptr, nullptr);
+        lsqr_residual<real><<<fb, LQ_THREADS, 0, s>>>(F, xt, bs, L->r, L->partials, L->counter, L->sc, 0);
+        launches += 2 * chunk + 2;
+        if (p->stop_rule == 1) {
+            lsqr_normal<real><<<bb, LQ_THREADS, 0, s>>>(B, L->r, L->partials, L->counter, L->sc, 0);
+            ++launches;
+        }
+        SME_CUDA(cudaGetLastError());
+        SME_CUDA(cudaMemcpyAsync(L->host, L->sc, sizeof(LsqrScalars), cudaMemcpyDeviceToHost, s));
+        SME_CUDA(cudaStreamSynchronize(s));
+        if (L->host->done) break;
+    }
+    // Final x in original order, and both residuals of exactly that x.
+    lsqr_current_x<real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, e, x, w, L->sc, xt, B.perm, x_out);
+    lsqr_residual<real><<<fb, LQ_THREADS, 0, s>>>(F, xt, bs, L->r, L->partials, L->counter, L->sc, 1);
+    lsqr_normal<real><<<bb, LQ_THREADS, 0, s>>>(B, L->r, L->partials, L->counter, L->sc, 1);
+    launches += 3;
+    SME_CUDA(cudaGetLastError());
+    SME_CUDA(cudaMemcpyAsync(L->host, L->sc, sizeof(LsqrScalars), cudaMemcpyDeviceToHost, s));
+    SME_CUDA(cudaStreamSynchronize(s));
+    const LsqrScalars &h = *L->host;
+    res->iters = h.iters;
+    res->rel_residual = h.rel_res;
+    res->normal_residual = h.normal_res;
+    const double final_metric = p->stop_rule == 1 ? h.normal_res : h.rel_res;
+    res->converged = (h.done != 0 && final_metric <= p->tol) || final_metric <= p->tol ? 1 : 0;
+    res->kernel_launches = launches;
+    if (!std::isfinite(h.rel_res)) {
+        set_error("sme_lsqr: residual became non-finite");
+        return SME_ERR_NONFINITE;
+    }
+    if (!res->converged) {
+        set_error("sme_lsqr: %lld iterations, residual %.3e above tol %.1e", (long long)h.iters, final_metric,
+                  p->tol);
+        return SME_ERR_NOT_CONVERGED;
+    }
+    return SME_OK;
+}
 
 }  // namespace sme
 
@@ -192,14 +704,18 @@ extern "C" sme_status sme_evaluate(sme_op op, const void *u, const void *v, doub
 extern "C" sme_status sme_lsqr(sme_op op, const void *u_bar, const void *v_bar, const void *b, void *x,
                                const sme_lsqr_params *p, sme_lsqr_result *res, void *stream)
 {
-    (void)op;
-    (void)u_bar;
-    (void)v_bar;
-    (void)b;
-    (void)x;
-    (void)p;
-    (void)res;
-    (void)stream;
-    set_error("sme_lsqr: not built yet");
-    return SME_ERR_UNSUPPORTED;
+    if (!op || !b || !x || !p || !res || p->max_iters < 0 || p->tol < 0 || (p->stop_rule != 0 && p->stop_rule != 1)) {
+        set_error("sme_lsqr: bad arguments");
+        return SME_ERR_ARG;
+    }
+    if (op->dense) {
+        set_error("sme_lsqr: dense operators are not supported");
+        return SME_ERR_UNSUPPORTED;
+    }
+    *res = sme_lsqr_result{};
+    if (op->dbl)
+        return lsqr_t<double>(op, (const double *)u_bar, (const double *)v_bar, (const double *)b, (double *)x, p, res,
+                              (cudaStream_t)stream);
+    return lsqr_t<float>(op, (const float *)u_bar, (const float *)v_bar, (const float *)b, (float *)x, p, res,
+                         (cudaStream_t)stream);
 }

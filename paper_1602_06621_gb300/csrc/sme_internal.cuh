@@ -133,6 +133,9 @@ struct sme_op_s {
     sme::DenseOp *dense = nullptr;
     int *d_status = nullptr;
     int64_t device_bytes = 0;
+    cudaEvent_t ev_loop[2] = {nullptr, nullptr};  // SME_EQ_TIMED
+    bool loop_timed = false;
+    int64_t loop_iters = 0;
 };
 
 namespace sme {

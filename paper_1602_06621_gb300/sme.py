@@ -15,14 +15,14 @@ import numpy as np
 from .build import LIB, build_library
 
 __all__ = [
-    "SmeError", "load", "SME_F64", "SME_F32", "SME_BF16", "SME_FP8E4M3", "SME_EQ_ASYNC", "SME_EQ_NO_GRAPH",
+    "SmeError", "load", "SME_F64", "SME_F32", "SME_BF16", "SME_FP8E4M3", "SME_EQ_ASYNC", "SME_EQ_NO_GRAPH", "SME_EQ_TIMED",
     "sme_op_create_csr", "sme_op_create_dense", "sme_op_destroy", "sme_op_get_info", "sme_draw_probes",
     "sme_equilibrate", "sme_op_check", "sme_estimate", "sme_evaluate", "sme_lsqr", "sme_status_string",
     "default_params",
 ]
 
 SME_F64, SME_F32, SME_BF16, SME_FP8E4M3 = 0, 1, 2, 3
-SME_EQ_ASYNC, SME_EQ_NO_GRAPH = 1, 2
+SME_EQ_ASYNC, SME_EQ_NO_GRAPH, SME_EQ_TIMED = 1, 2, 4
 _STATUS = {0: "SME_OK", -1: "SME_ERR_ARG", -2: "SME_ERR_INVALID_CSR", -3: "SME_ERR_OOM", -4: "SME_ERR_CUDA",
            -5: "SME_ERR_NONFINITE", -6: "SME_ERR_TIMEOUT", -7: "SME_ERR_NOT_CONVERGED", -8: "SME_ERR_UNSUPPORTED"}
 
@@ -44,7 +44,8 @@ class sme_equil_params(ctypes.Structure):
 class sme_op_info(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("dtype", ctypes.c_int32),
                 ("state_is_double", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
-                ("padded_entries_fwd", ctypes.c_int64), ("padded_entries_bwd", ctypes.c_int64)]
+                ("padded_entries_fwd", ctypes.c_int64), ("padded_entries_bwd", ctypes.c_int64),
+                ("last_loop_ms", ctypes.c_double), ("last_loop_iters", ctypes.c_int64)]
 
 
 class sme_eval_result(ctypes.Structure):
@@ -59,7 +60,7 @@ class sme_lsqr_params(ctypes.Structure):
 
 class sme_lsqr_result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("rel_residual", ctypes.c_double), ("normal_residual", ctypes.c_double),
-                ("converged", ctypes.c_int32)]
+                ("converged", ctypes.c_int32), ("kernel_launches", ctypes.c_int64)]
 
 
 _lib = None

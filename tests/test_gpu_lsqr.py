@@ -1,0 +1,136 @@
+"""GPU LSQR (Section 5.1) against the FP64 oracle's LSQR, through the C ABI.
+
+LSQR is a Lanczos process: two correct implementations that round differently
+drift apart as orthogonality is lost, so iterates are compared over the first
+few iterations (where rounding has not been amplified), and longer solves are
+judged by what LSQR promises: the residual of the returned x.  The residual the
+library reports is re-computed here from its x by the oracle in FP64.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1602_06621_gb300 import inputs as I
+from paper_1602_06621_gb300 import sme
+
+from gpu_util import gpu_equilibrate, make_op
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_lsqr(op, dt, ub, vb, b, n, **kw):
+    import torch
+    td = torch.float64 if dt == sme.SME_F64 else torch.float32
+    t = lambda a: None if a is None else torch.as_tensor(np.asarray(a), device="cuda").to(td)
+    x = torch.full((n,), float("nan"), dtype=td, device="cuda")
+    res = sme.sme_lsqr(op, t(ub), t(vb), t(b), x, **kw)
+    torch.cuda.synchronize()
+    return x.cpu().double().numpy(), res
+
+
+def _oracle_lsqr(A, ub, vb, b, iters, **kw):
+    import scipy.sparse as sp
+    S = sp.csr_matrix((A.vals.astype(np.float64), A.col_idx, A.row_ptr), shape=(A.m, A.n))
+    d = np.exp(ub) if ub is not None else np.ones(A.m)
+    e = np.exp(vb) if vb is not None else np.ones(A.n)
+    K = sp.diags(d) @ S @ sp.diags(e)
+    r = O.lsqr(lambda x: K @ x, lambda y: K.T @ y, d * b, A.n, max_iters=iters, **kw)
+    return e * r.x, r
+
+
+def _rel_res(A, x, b):
+    return np.linalg.norm(O.csr_matvec(A, x) - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def small():
+    A = I.workload_small(1)
+    op, dt = make_op(A)
+    yield A, op, dt
+    sme.sme_op_destroy(op)
+
+
+@pytest.mark.parametrize("scaled", [False, True])
+@pytest.mark.parametrize("iters", [1, 3, 6])
+def test_early_iterates_match_oracle_fp64(small, scaled, iters):
+    A, op, dt = small
+    b = I.normal_vector(A.m, 5)
+    ub = vb = None
+    if scaled:
+        _, _, ub, vb = O.equilibrate(A, T=30, k=1, seed=0)
+    x, res = _gpu_lsqr(op, dt, ub, vb, b, A.n, tol=0.0, max_iters=iters, check_every=iters)
+    xo, _ = _oracle_lsqr(A, ub, vb, b, iters)
+    assert res["iters"] == iters
+    assert np.linalg.norm(x - xo) <= 1e-9 * np.linalg.norm(xo)
+
+
+def test_consistent_system_converges_and_reports_its_residual(small):
+    """b = A x*: LSQR on D A E reaches ||Ax - b|| / ||b|| <= 1e-6 in FP64, in about as many
+    iterations as the oracle's LSQR, and the residual it reports is that of the x it returns."""
+    A, op, dt = small
+    b = O.csr_matvec(A, I.normal_vector(A.n, 6))
+    _, _, ub, vb = gpu_equilibrate(op, dt, A.m, A.n, T=200, k=1, seed=0)
+    x, res = _gpu_lsqr(op, dt, ub, vb, b, A.n, tol=1e-6, max_iters=20000, check_every=1)
+    assert res["converged"] == 1 and res["rel_residual"] <= 1e-6
+    assert res["rel_residual"] == pytest.approx(_rel_res(A, x, b), rel=1e-9)
+    _, ro = _oracle_lsqr(A, ub, vb, b, 20000, residual=lambda xb: _rel_res(A, np.exp(vb) * xb, b), tol=1e-6)
+    assert ro.converged and abs(res["iters"] - ro.iters) <= max(3, 0.1 * ro.iters)
+
+
+def test_equilibration_cuts_gpu_lsqr_iterations(small):
+    """Section 5.1 on the GPU: the equilibrated system needs far fewer LSQR iterations."""
+    A, op, dt = small
+    b = O.csr_matvec(A, I.normal_vector(A.n, 6))
+    _, _, ub, vb = gpu_equilibrate(op, dt, A.m, A.n, T=200, k=1, seed=0)
+    _, pre = _gpu_lsqr(op, dt, ub, vb, b, A.n, tol=1e-6, max_iters=50000, check_every=10)
+    _, plain = _gpu_lsqr(op, dt, None, None, b, A.n, tol=1e-6, max_iters=50000, check_every=10)
+    assert pre["converged"] == 1
+    assert plain["iters"] > 10 * (pre["iters"] + 200)
+
+
+def test_least_squares_with_column_scaling_fp64(small):
+    """b ~ N(0,1) is inconsistent; column scaling alone (u_bar = NULL) keeps the least-squares
+    minimiser, and LSQR stops on the normal-equation residual."""
+    A, op, dt = small
+    b = I.normal_vector(A.m, 7)
+    _, _, _, vb = gpu_equilibrate(op, dt, A.m, A.n, T=200, k=1, seed=0)
+    x, res = _gpu_lsqr(op, dt, None, vb, b, A.n, tol=1e-6, max_iters=50000, check_every=5, stop_rule=1)
+    assert res["converged"] == 1 and res["normal_residual"] <= 1e-6
+    D = A.to_dense()
+    xls = np.linalg.lstsq(D, b, rcond=None)[0]
+    r = D @ x - b
+    assert np.linalg.norm(D.T @ r) / (np.linalg.norm(D) * np.linalg.norm(r)) <= 1.01e-6
+    # ||r||^2 = ||r_ls||^2 + ||A (x - x_ls)||^2: the residual is within rounding of the minimum.
+    assert np.linalg.norm(r) <= (1 + 1e-6) * np.linalg.norm(D @ xls - b)
+
+
+def test_fp32_solve_on_the_large_family():
+    """FP32 vectors and products, FP64 scalars and checks: 1e-6 on the scaled-down large workload."""
+    A = I.workload_large(scale=0.01, seed=4)
+    op, dt = make_op(A)
+    try:
+        b = O.csr_matvec(O.OracleCSR.from_any(A), I.normal_vector(A.n, 8)).astype(np.float32)
+        _, _, ub, vb = gpu_equilibrate(op, dt, A.m, A.n, T=500, k=32, seed=0)
+        x, res = _gpu_lsqr(op, dt, ub, vb, b, A.n, tol=1e-6, max_iters=5000, check_every=10)
+    finally:
+        sme.sme_op_destroy(op)
+    assert res["converged"] == 1
+    A64 = O.OracleCSR.from_any(A)
+    b64 = b.astype(np.float64)
+    assert res["rel_residual"] == pytest.approx(_rel_res(A64, x, b64), rel=1e-6)
+    assert res["iters"] < 200
+
+
+def test_zero_right_hand_side(small):
+    A, op, dt = small
+    x, res = _gpu_lsqr(op, dt, None, None, np.zeros(A.m), A.n, tol=1e-6, max_iters=100)
+    assert np.all(x == 0) and res["converged"] == 1 and res["iters"] == 0
+
+
+def test_not_converged_is_reported(small):
+    A, op, dt = small
+    b = O.csr_matvec(A, I.normal_vector(A.n, 6))
+    with pytest.raises(sme.SmeError) as ei:
+        _gpu_lsqr(op, dt, None, None, b, A.n, tol=1e-12, max_iters=20, check_every=10,
+                  raise_on_not_converged=True)
+    assert ei.value.name == "SME_ERR_NOT_CONVERGED"
