@@ -232,12 +232,25 @@ def main():
     x = torch.zeros(n, **f32)
     do_lsqr = not args.no_lsqr
 
-    def step():
+    ev_mid = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    phase_ms = {"equilibrate": [], "lsqr": []}
+
+    def step(record=False):
+        stream = torch.cuda.current_stream()
+        if record:
+            ev_mid[0].record(stream)
         u.zero_(), v.zero_(), ub.zero_(), vb.zero_()
         sme.sme_equilibrate(op, u, v, ub, vb, T=T, k=k, seed=0, flags=sme.SME_EQ_TIMED | sme.SME_EQ_ASYNC)
+        if record:
+            ev_mid[1].record(stream)
         res = None
         if do_lsqr:
             res = sme.sme_lsqr(op, ub, vb, b, x, tol=1e-6, max_iters=20000, check_every=10)
+        if record:
+            ev_mid[2].record(stream)
+            ev_mid[2].synchronize()
+            phase_ms["equilibrate"].append(ev_mid[0].elapsed_time(ev_mid[1]))
+            phase_ms["lsqr"].append(ev_mid[1].elapsed_time(ev_mid[2]))
         return res
 
     for _ in range(args.warmup):
@@ -251,7 +264,7 @@ def main():
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
-            r = step()
+            r = step(record=True)
             loop_ms.append(sme.sme_op_get_info(op)["last_loop_ms"])
             if r is not None:
                 lsqr_res.append(r)
@@ -271,7 +284,21 @@ def main():
     bytes_iter = algorithmic_bytes_per_iteration(m, n, nnz)
     peak, peak_kind = measured_hbm_peak()
     achieved = bytes_iter / iter_s / 1e9
-    launches_per_step = T + 4 + (lsqr_res[0]["gpu_launches"] if lsqr_res and "gpu_launches" in lsqr_res[0] else 0)
+    launches_per_step = T + 4
+    gpu_launches = launches_per_step * args.steps + sum(int(r["kernel_launches"]) for r in lsqr_res)
+
+    # Plain LSQR (no equilibration) on the same system, once, outside the timed region.
+    plain = None
+    if do_lsqr:
+        cap = 20000
+        pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        xp = torch.zeros(n, **f32)
+        pe0.record(torch.cuda.current_stream())
+        pr = sme.sme_lsqr(op, None, None, b, xp, tol=1e-6, max_iters=cap, check_every=100)
+        pe1.record(torch.cuda.current_stream())
+        pe1.synchronize()
+        plain = {"iters": int(pr["iters"]), "rel_residual": pr["rel_residual"], "converged": bool(pr["converged"]),
+                 "ms": pe0.elapsed_time(pe1), "iteration_cap": cap}
 
     # Quality of the last step's scaling (outside the timed region).
     quality = sme.sme_evaluate(op, ub, vb)
@@ -335,7 +362,7 @@ def main():
                          "algorithmic_bytes_per_launch": bytes_iter, "launch_us": iter_s * 1e6},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches": gpu_launches,
             "clocks": clocks,
             "equilibration": {"iteration_us": iter_s * 1e6, "probe_pairs_per_s_loop": k / iter_s,
                               "hbm_gbs": achieved, "row_spread": quality["row_spread"],
@@ -344,7 +371,12 @@ def main():
         }
         if lsqr_res:
             last = lsqr_res[-1]
-            line["lsqr"] = {k2: last[k2] for k2 in ("iters", "rel_residual", "converged")}
+            eq_ms = statistics.median(phase_ms["equilibrate"])
+            ls_ms = statistics.median(phase_ms["lsqr"])
+            line["lsqr"] = {"iters": int(last["iters"]), "rel_residual": last["rel_residual"],
+                            "converged": bool(last["converged"]), "ms": ls_ms,
+                            "time_to_1e-6_ms": eq_ms + ls_ms, "equilibrate_ms": eq_ms,
+                            "plain": plain}
         print(json.dumps(line), flush=True)
     sme.sme_op_destroy(op)
     if dist is not None:
