@@ -215,6 +215,35 @@ typedef struct {
 sme_status sme_lsqr(sme_op op, const void *u_bar, const void *v_bar, const void *b, void *x,
                     const sme_lsqr_params *p, sme_lsqr_result *res, void *stream);
 
+/* ------------------------------------------------------------------ allocation-free estimator */
+
+/*
+ * sme_estimate_rows_static -- the row-side estimate of sme_estimate (z_u only, FP32),
+ * for callers that must not allocate device memory on this path: code recording
+ * into a CUDA graph, code whose device memory is already owned by a caching
+ * allocator, or a latency-critical loop that cannot take the synchronisation an
+ * allocation or a free may cause.  The paper has no counterpart: this is a
+ * property of the library, not of the method.
+ *
+ * Works directly on the caller's device CSR (row_ptr int32[m+1], col_idx int32[nnz],
+ * vals float[nnz]) and device vectors u[m], v[n]; writes z_u[m].  Probes as in
+ * sme_estimate (iteration t, Philox stream stream_base for s).  k in {1,2,4,...,32}.
+ *
+ * Calls no cudaMalloc/cudaFree.  Its only scratch, a gather table of n entries,
+ * is a fixed array of SME_STATIC_MAX_COLS entries (8 bytes each) inside the
+ * library; every GPU that loads the library holds it until the process exits.
+ * n > SME_STATIC_MAX_COLS returns SME_ERR_ARG.  All calls on a device share the
+ * array: calls whose GPU work overlaps (unordered streams) race on it.  The first
+ * call on each device looks up the array's device address (cudaGetSymbolAddress),
+ * so make that first call before beginning any stream capture.  The CSR is not
+ * validated here (pass one sme_op_create_csr would accept).
+ */
+#define SME_STATIC_MAX_COLS (1 << 20)
+
+sme_status sme_estimate_rows_static(int64_t m, int64_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                                    const float *vals, const float *u, const float *v, int32_t t, int32_t k,
+                                    uint64_t seed, int32_t stream_base, float *z_u, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,8 +18,9 @@ __all__ = [
     "SmeError", "load", "SME_F64", "SME_F32", "SME_BF16", "SME_FP8E4M3", "SME_EQ_ASYNC", "SME_EQ_NO_GRAPH", "SME_EQ_TIMED",
     "sme_op_create_csr", "sme_op_create_dense", "sme_op_destroy", "sme_op_get_info", "sme_draw_probes",
     "sme_equilibrate", "sme_op_check", "sme_estimate", "sme_evaluate", "sme_lsqr", "sme_status_string",
-    "default_params",
+    "default_params", "sme_estimate_rows_static", "SME_STATIC_MAX_COLS",
 ]
+SME_STATIC_MAX_COLS = 1 << 20
 
 SME_F64, SME_F32, SME_BF16, SME_FP8E4M3 = 0, 1, 2, 3
 SME_EQ_ASYNC, SME_EQ_NO_GRAPH, SME_EQ_TIMED = 1, 2, 4
@@ -81,6 +82,7 @@ SIGNATURES = {
     "sme_evaluate": ([_vp, _vp, _vp, _d, _d, _d, _vp, _vp, ctypes.POINTER(sme_eval_result), _vp], _i32),
     "sme_lsqr": ([_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(sme_lsqr_params), ctypes.POINTER(sme_lsqr_result), _vp],
                  _i32),
+    "sme_estimate_rows_static": ([_i64, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _u64, _i32, _vp, _vp], _i32),
 }
 
 
@@ -212,3 +214,10 @@ def sme_lsqr(op, u_bar, v_bar, b, x, *, tol=1e-6, max_iters=100000, check_every=
     if st != -7 or raise_on_not_converged:
         _check(st, "sme_lsqr")
     return {f: getattr(res, f) for f, _ in sme_lsqr_result._fields_}
+
+
+def sme_estimate_rows_static(m, n, row_ptr, col_idx, vals, u, v, t, k, seed, stream_base, z_u, stream=None):
+    """Row estimate without any device allocation (see include/sme.h); all arguments are CUDA tensors."""
+    _check(load().sme_estimate_rows_static(int(m), int(n), _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(u), _ptr(v),
+                                           int(t), int(k), int(seed), int(stream_base), _ptr(z_u), _stream(stream)),
+           "sme_estimate_rows_static")
