@@ -28,7 +28,7 @@ from .build import build_oracle
 
 __all__ = [
     "lib", "philox4x32_10", "probe_signs", "row_estimate", "col_estimate", "psgd_step", "equilibrate",
-    "psgd_step_sampled", "exact_norms_sq", "csr_matvec", "default_params", "objective", "gradient",
+    "psgd_step_sampled", "exact_norms_sq", "csr_matvec", "dense_estimate_sampled", "default_params", "objective", "gradient",
     "rms_error", "spread", "log_phi", "kappa", "sinkhorn_knopp", "block_minimize_u", "block_minimize_v",
     "regularized_optimum", "lsqr", "LsqrResult", "OracleCSR",
 ]
@@ -60,6 +60,8 @@ def lib():
                                            _i32, _dp, _dp, _dp, _dp, _i64, _i64p, _i64, _i64p, _dp, _dp, _dp, _dp]
         L.or_exact_norms_sq.argtypes = [_i64, _i64, _i64p, _i32p, _dp, _dp, _dp, _dp, _dp]
         L.or_csr_matvec.argtypes = [_i64, _i64p, _i32p, _dp, _dp, _dp]
+        L.or_dense_estimate_sampled.argtypes = [_i64, _i64, ctypes.POINTER(ctypes.c_float), _dp, _dp, _dp, _i32, _i32,
+                                                _u64, _i32, _i64, _i64p, _i64, _i64p, _dp, _dp]
         _LIB = L
     return _LIB
 
@@ -214,6 +216,21 @@ def exact_norms_sq(A, u, v):
     lib().or_exact_norms_sq(A.m, A.n, _p(A.row_ptr, _i64p), _p(A.col_idx, _i32p), _p(A.vals, _dp),
                             _p(_f64(u), _dp), _p(_f64(v), _dp), _p(r2, _dp), _p(c2, _dp))
     return r2, c2
+
+
+def dense_estimate_sampled(A, u, v, rows, cols, *, t, k, seed, stream_base=0, row_scale=None):
+    """Estimates of iteration t for dense A at the listed rows and columns (FP64 accumulation)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    m, n = A.shape
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    zu, zv = np.zeros(rows.size), np.zeros(cols.size)
+    rs = None if row_scale is None else _f64(row_scale)
+    lib().or_dense_estimate_sampled(m, n, A.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                    None if rs is None else _p(rs, _dp), _p(_f64(u), _dp), _p(_f64(v), _dp), t, k, seed,
+                                    stream_base, rows.size, _p(rows, _i64p), cols.size, _p(cols, _i64p),
+                                    _p(zu, _dp), _p(zv, _dp))
+    return zu, zv
 
 
 def csr_matvec(A, x):

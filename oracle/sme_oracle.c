@@ -272,3 +272,53 @@ void or_csr_matvec(int64_t m, const int64_t *row_ptr, const int32_t *col, const 
         y[i] = acc;
     }
 }
+
+/* Dense A (m x n, row-major, float values widened to FP64): the estimates of iteration t at the listed
+ * rows and columns, with sign tables s (n x k) and w (m x k) drawn once from Philox.
+ *   zu[q] = (1/k) sum_p (sum_j e^{u_i} A_ij e^{v_j} s_jp)^2   for i = rows[q]
+ *   zv[q] = (1/k) sum_p (sum_i e^{v_j} A_ij e^{u_i} w_ip)^2   for j = cols[q]
+ * row_scale (nullable) multiplies row i of A. */
+void or_dense_estimate_sampled(int64_t m, int64_t n, const float *A, const double *row_scale, const double *u,
+                               const double *v, int32_t t, int32_t k, uint64_t seed, int32_t stream_base,
+                               int64_t n_rows, const int64_t *rows, int64_t n_cols, const int64_t *cols,
+                               double *zu, double *zv)
+{
+    double *s = (double *)malloc((size_t)(n * k) * sizeof(double));
+    double *w = (double *)malloc((size_t)(m * k) * sizeof(double));
+    or_draw_probes(seed, t, stream_base, n, k, s);
+    or_draw_probes(seed, t, stream_base + 1, m, k, w);
+    double *y = (double *)malloc((size_t)k * sizeof(double));
+    for (int64_t q = 0; q < n_rows; ++q) {
+        int64_t i = rows[q];
+        double ci = row_scale ? row_scale[i] : 1.0;
+        for (int32_t p = 0; p < k; ++p)
+            y[p] = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double b = exp(u[i]) * ci * (double)A[i * n + j] * exp(v[j]);
+            for (int32_t p = 0; p < k; ++p)
+                y[p] += b * s[j * k + p];
+        }
+        double acc = 0.0;
+        for (int32_t p = 0; p < k; ++p)
+            acc += y[p] * y[p];
+        zu[q] = acc / (double)k;
+    }
+    for (int64_t q = 0; q < n_cols; ++q) {
+        int64_t j = cols[q];
+        for (int32_t p = 0; p < k; ++p)
+            y[p] = 0.0;
+        for (int64_t i = 0; i < m; ++i) {
+            double ci = row_scale ? row_scale[i] : 1.0;
+            double b = exp(v[j]) * ci * (double)A[i * n + j] * exp(u[i]);
+            for (int32_t p = 0; p < k; ++p)
+                y[p] += b * w[i * k + p];
+        }
+        double acc = 0.0;
+        for (int32_t p = 0; p < k; ++p)
+            acc += y[p] * y[p];
+        zv[q] = acc / (double)k;
+    }
+    free(y);
+    free(s);
+    free(w);
+}

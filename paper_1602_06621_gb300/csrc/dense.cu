@@ -1,36 +1,706 @@
-// Dense operator: products with +-1 probe blocks on the tensor cores.
+// Dense operator: the probe products of Algorithm 1 on the tcgen05 tensor cores.
+//
+// For dense A (m x n) one iteration needs Y = A (E S) and Y' = A^T (D W) with S (n x k), W (m x k)
+// of +-1 probes (Section 3.1 estimator).  The +-1 entries are exact in BF16, but e^{v_j} s_jp is not,
+// so each B operand holds two BF16 terms: B = [hi | lo] with hi = bf16(x), lo = bf16(x - hi), and the
+// two accumulators are added in the epilogue (relative error of the scaling ~2^-17 instead of 2^-9).
+//
+// Both products are the same GEMM, X (M x K, row-major BF16) times B^T (N x K, row-major BF16):
+// the op keeps A and a transposed copy A^T, so every operand is K-major.  One launch performs one
+// iteration: CTAs [0, m/128) take 128-row tiles of A (forward), the others 128-row tiles of A^T.
+// Each CTA owns its full output tile (128 x 2k FP32 in TMEM, 2k <= 512 columns), streams K through a
+// two-stage TMA pipeline (128-byte swizzle), one thread issues tcgen05.mma, and four epilogue warps
+// read TMEM and finish the row in registers: z = e^{2x} (1/k) sum_p (hi_p + lo_p)^2, the projected
+// step, the running average, and the row's slice of the NEXT iteration's B operand (its scale and
+// Philox probe bits), double-buffered like the sparse path's gather tables.
+//
+// Every wait on an mbarrier is bounded: on expiry the kernel sets ST_TIMEOUT in the op's status word,
+// waits (bounded) for its own outstanding copies and MMAs, frees its TMEM and returns.
 
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
 
 #include "sme_internal.cuh"
 
 namespace sme {
 
-void dense_destroy(sme_op op) { op->dense = nullptr; }
+constexpr int DN_BM = 128;           // rows per tile (MMA M)
+constexpr int DN_BK = 64;            // K per stage: 64 BF16 = one 128-byte swizzle row
+constexpr int DN_STAGES = 2;
+constexpr int DN_THREADS = 192;      // warp 0 TMA, warp 1 MMA + TMEM owner, warps 2..5 epilogue
+constexpr uint32_t DN_WAIT_LIMIT = 1u << 22;  // polls of a try_wait before a wait is abandoned
+
+struct DenseOp {
+    bool fp8 = false;
+    int64_t m = 0, n = 0;
+    __nv_bfloat16 *A = nullptr, *At = nullptr;  // row-major m x n and n x m
+    float *row_scale = nullptr;                 // FP8 input: per-row scales (applied in the epilogue)
+    __nv_bfloat16 *Bf[2] = {nullptr, nullptr};  // [2k][n]: forward operand (columns' scale x probes)
+    __nv_bfloat16 *Bb[2] = {nullptr, nullptr};  // [2k][m]: backward operand
+    int kcap = 0;
+    float *x[2] = {nullptr, nullptr}, *xb[2] = {nullptr, nullptr};  // u, ubar / v, vbar
+    CUtensorMap mapA, mapAt, mapBf[2], mapBb[2];
+};
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of `bar`; false if it did not complete within the limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < DN_WAIT_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void *p)
+{
+    const uint64_t addr = smem_u32(p);
+    uint64_t d = 0;
+    d |= (addr >> 4) & 0x3FFFull;          // start address
+    d |= (uint64_t)1 << 16;                // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;      // stride byte offset: 8 rows x 128 bytes
+    d |= (uint64_t)1 << 46;                // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                // swizzle mode: 128 bytes
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------------ the iteration kernel
+
+struct DenseArgs {
+    int64_t m, n;
+    int row_tiles;            // m / 128; CTAs beyond are column tiles
+    int kp;                   // probes (128 or 256)
+    float *x[2], *xb[2];      // [0] u, ubar (rows)   [1] v, vbar (columns)
+    float *z[2];              // estimate-only outputs, or null
+    __nv_bfloat16 *bnext[2];  // [0] next backward operand (written by rows), [1] next forward operand
+    float target2[2];
+    float gamma, M, eta, avg_new, avg_old;
+    uint32_t t_next, key0, key1, sid_out[2];
+    int mode;                 // 0 step, 1 estimate only
+    const float *row_scale;   // A_ij = row_scale[i] * Abf16_ij (FP8 input), or null
+    int *status;
+};
+
+struct DenseMaps {
+    CUtensorMap X[2];  // [0] A, [1] A^T
+    CUtensorMap B[2];  // [0] forward operand (current), [1] backward operand (current)
+};
+
+template <int KP>
+__global__ void __launch_bounds__(DN_THREADS, 1) dense_iteration(const __grid_constant__ DenseMaps maps, DenseArgs a)
+{
+    constexpr int NT = 2 * KP;                       // accumulator columns: hi then lo
+    constexpr int A_BYTES = DN_BM * DN_BK * 2;       // 16 KB
+    constexpr int B_BYTES = NT * DN_BK * 2;          // 32 or 64 KB
+    constexpr int STAGE = A_BYTES + B_BYTES;
+    constexpr uint32_t IDESC = idesc_bf16(DN_BM, 256);
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t full_bar[DN_STAGES], empty_bar[DN_STAGES], acc_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh, issued_sh, consumed_sh;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool cols = (int)blockIdx.x >= a.row_tiles;
+    const int tile = cols ? (int)blockIdx.x - a.row_tiles : (int)blockIdx.x;
+    const int64_t K = cols ? a.m : a.n;              // reduction length
+    const int nk = (int)(K / DN_BK);
+    const CUtensorMap *mapX = cols ? &maps.X[1] : &maps.X[0];
+    const CUtensorMap *mapB = cols ? &maps.B[1] : &maps.B[0];
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < DN_STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&acc_bar, 1);
+        abort_sh = 0;
+        issued_sh = 0;
+        consumed_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"((uint32_t)NT));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+
+    int issued_mma = 0;  // MMA issuer: stages whose MMAs were issued
+    if (warp == 0 && lane == 0) {
+        // TMA producer.
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % DN_STAGES;
+            if (kb >= DN_STAGES && !mbar_wait(&empty_bar[s], ((kb / DN_STAGES) - 1) & 1)) {
+                atomicOr(a.status, ST_TIMEOUT);
+                atomicExch(&abort_sh, 1);
+                break;
+            }
+            if (*(volatile int *)&abort_sh) break;
+            uint8_t *sa = smem + s * STAGE;
+            uint8_t *sb = sa + A_BYTES;
+            mbar_expect_tx(&full_bar[s], STAGE);
+            tma_load_2d(sa, mapX, kb * DN_BK, tile * DN_BM, &full_bar[s]);
+            for (int h = 0; h < NT / 256; ++h) tma_load_2d(sb + h * 256 * 128, mapB, kb * DN_BK, h * 256, &full_bar[s]);
+            issued_sh = kb + 1;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer.
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % DN_STAGES;
+            if (!mbar_wait(&full_bar[s], (kb / DN_STAGES) & 1)) {
+                atomicOr(a.status, ST_TIMEOUT);
+                atomicExch(&abort_sh, 1);
+                break;
+            }
+            if (*(volatile int *)&abort_sh) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint8_t *sa = smem + s * STAGE;
+            uint8_t *sb = sa + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < DN_BK / 16; ++kk) {
+                const uint64_t ad = smem_desc_sw128(sa) + (uint64_t)(kk * 2);  // +32 bytes along K
+#pragma unroll
+                for (int h = 0; h < NT / 256; ++h) {
+                    const uint64_t bd = smem_desc_sw128(sb + h * 256 * 128) + (uint64_t)(kk * 2);
+                    mma_bf16(tmem + h * 256, ad, bd, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
+                }
+            }
+            mma_commit(&empty_bar[s]);
+            ++issued_mma;
+            consumed_sh = kb + 1;
+        }
+        mma_commit(&acc_bar);  // arrives once every MMA issued above has completed
+    }
+
+    // Epilogue: warps 2..5, one TMEM lane (one row of the tile) per thread.
+    if (warp >= 2) {
+        const bool ok = mbar_wait(&acc_bar, 0);
+        if (!ok) atomicOr(a.status, ST_TIMEOUT);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        const int64_t r = (int64_t)tile * DN_BM + row;
+        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16);
+        float ss = 0.f;
+#pragma unroll 1
+        for (int c = 0; c < KP / 32; ++c) {
+            float hi[32], lo[32];
+            tmem_ld32(taddr + c * 32, hi);
+            tmem_ld32(taddr + KP + c * 32, lo);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const float y = hi[i] + lo[i];
+                ss += y * y;
+            }
+        }
+        const int side = cols ? 1 : 0;
+        if (ok && !*(volatile int *)&abort_sh) {
+            float *X = a.x[side];
+            const float xo = X[r];
+            const float ex = expf(xo);
+            // With row scales A = diag(c) A', row i of D A E is c_i times row i of D A' E, and the
+            // backward operand carries c_i (see below), so only the rows' estimate needs c_i^2.
+            const float ci = (!cols && a.row_scale) ? a.row_scale[r] : 1.f;
+            const float z = ex * ex * ci * ci * ss * (1.f / (float)KP);
+            if (a.mode == 1) {
+                a.z[side][r] = z;
+            } else {
+                float xn = xo - a.eta * (z - a.target2[side] + a.gamma * xo);
+                if (!isfinite(xn)) atomicOr(a.status, ST_NONFINITE);
+                xn = fminf(fmaxf(xn, -a.M), a.M);
+                X[r] = xn;
+                float *XB = a.xb[side];
+                XB[r] = a.avg_new * xn + a.avg_old * XB[r];
+                // This row's entries of the next iteration's operand: scale e^{x^t} times probes of t+1.
+                const float sc = expf(xn) * ((!cols && a.row_scale) ? a.row_scale[r] : 1.f);
+                const __nv_bfloat16 hi = __float2bfloat16_rn(sc);
+                const __nv_bfloat16 lo = __float2bfloat16_rn(sc - __bfloat162float(hi));
+                const int64_t ld = cols ? a.n : a.m;
+                __nv_bfloat16 *Bn = a.bnext[side];
+                for (int g = 0; g < KP / 128; ++g) {
+                    const U4 o = philox10(U4{(uint32_t)r, a.t_next, a.sid_out[side], (uint32_t)g}, a.key0, a.key1);
+                    const uint32_t words[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll 4
+                    for (int p = 0; p < 128; ++p) {
+                        const bool neg = (words[p >> 5] >> (p & 31)) & 1u;
+                        const int pp = g * 128 + p;
+                        Bn[(int64_t)pp * ld + r] = neg ? __hneg(hi) : hi;
+                        Bn[(int64_t)(KP + pp) * ld + r] = neg ? __hneg(lo) : lo;
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // After an abandoned wait: let copies that were issued but never consumed land before exiting.
+        for (int kb = consumed_sh; kb < issued_sh; ++kb) mbar_wait(&full_bar[kb % DN_STAGES], (kb / DN_STAGES) & 1);
+    }
+    if (warp == 1) {
+        // MMAs still in flight must finish before their TMEM is released (bounded; completes at once normally).
+        if (lane == 0) mbar_wait(&acc_bar, 0);
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)NT));
+    }
+    (void)issued_mma;
+}
+
+// Operand of iteration t from a state vector: B[p][i] = s_ip * hi(e^{x_i}), B[k+p][i] = s_ip * lo(e^{x_i}).
+__global__ void dense_build_operand(int64_t len, int kp, const float *x, const float *mult, uint32_t t, uint32_t sid,
+                                    uint32_t k0, uint32_t k1, __nv_bfloat16 *B)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    const float sc = expf(x[i]) * (mult ? mult[i] : 1.f);
+    const __nv_bfloat16 hi = __float2bfloat16_rn(sc);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(sc - __bfloat162float(hi));
+    for (int g = 0; g < kp / 128; ++g) {
+        const U4 o = philox10(U4{(uint32_t)i, t, sid, (uint32_t)g}, k0, k1);
+        const uint32_t words[4] = {o.x, o.y, o.z, o.w};
+        for (int p = 0; p < 128; ++p) {
+            const bool neg = (words[p >> 5] >> (p & 31)) & 1u;
+            const int pp = g * 128 + p;
+            B[(int64_t)pp * len + i] = neg ? __hneg(hi) : hi;
+            B[(int64_t)(kp + pp) * len + i] = neg ? __hneg(lo) : lo;
+        }
+    }
+}
+
+// 32x32 tiled transpose of a BF16 matrix (rows x cols) into (cols x rows).
+__global__ void transpose_bf16(const __nv_bfloat16 *in, int64_t rows, int64_t cols, __nv_bfloat16 *out)
+{
+    __shared__ __nv_bfloat16 t[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int64_t r = r0 + j, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) t[j][threadIdx.x] = in[r * cols + c];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int64_t c = c0 + j, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) out[c * rows + r] = t[threadIdx.x][j];
+    }
+}
+
+// FP8 (e4m3) input -> BF16.  Every e4m3 value is exactly representable in BF16 (3 of its 7 mantissa
+// bits, exponents -9..8), so the tensor-core operand is the FP8 matrix itself; row scales stay separate.
+__global__ void fp8_to_bf16(const uint8_t *in, int64_t m, int64_t n, int64_t lda, __nv_bfloat16 *out)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m * n) return;
+    const int64_t i = idx / n, j = idx % n;
+    const uint8_t b = in[i * lda + j];
+    // e4m3: 1 sign, 4 exponent (bias 7), 3 mantissa; 0x7f / 0xff are NaN.
+    const int s = b >> 7, e = (b >> 3) & 15, f = b & 7;
+    float v;
+    if ((b & 0x7f) == 0x7f) v = NAN;
+    else if (e == 0) v = ldexpf((float)f, -9);
+    else v = ldexpf((float)(8 + f), e - 10);
+    if (s) v = -v;
+    out[idx] = __float2bfloat16_rn(v);
+}
+
+__global__ void bf16_check_finite(const __nv_bfloat16 *a, int64_t count, int *status)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(__bfloat162float(a[i]))) atomicOr(status, ST_BAD_VALUE);
+}
+
+// ------------------------------------------------------------------ host side
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// Row-major BF16 matrix (rows x cols) viewed with boxes of 64 columns (128 bytes) x box_rows rows.
+static sme_status make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int box_rows)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) {
+        set_error("cuTensorMapEncodeTiled unavailable");
+        return SME_ERR_CUDA;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return SME_ERR_CUDA;
+    }
+    return SME_OK;
+}
+
+static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+static size_t dense_smem(int kp) { return (size_t)DN_STAGES * (DN_BM * DN_BK * 2 + 2 * kp * DN_BK * 2) + 1024; }
+
+static sme_status ensure_dense_workspace(sme_op op, int kp)
+{
+    DenseOp *D = op->dense;
+    if (D->kcap >= kp) return SME_OK;
+    for (int b = 0; b < 2; ++b) {
+        if (D->Bf[b]) cudaFree(D->Bf[b]);
+        if (D->Bb[b]) cudaFree(D->Bb[b]);
+        D->Bf[b] = D->Bb[b] = nullptr;
+        SME_TRY(dev_alloc(op, (void **)&D->Bf[b], (size_t)2 * kp * D->n * 2));
+        SME_TRY(dev_alloc(op, (void **)&D->Bb[b], (size_t)2 * kp * D->m * 2));
+        SME_TRY(make_map(&D->mapBf[b], D->Bf[b], 2 * kp, D->n, 256));
+        SME_TRY(make_map(&D->mapBb[b], D->Bb[b], 2 * kp, D->m, 256));
+    }
+    if (!D->x[0]) {
+        SME_TRY(dev_alloc(op, (void **)&D->x[0], D->m * 4));
+        SME_TRY(dev_alloc(op, (void **)&D->xb[0], D->m * 4));
+        SME_TRY(dev_alloc(op, (void **)&D->x[1], D->n * 4));
+        SME_TRY(dev_alloc(op, (void **)&D->xb[1], D->n * 4));
+    }
+    D->kcap = kp;
+    return SME_OK;
+}
+
+template <int KP>
+static sme_status launch_dense(const DenseMaps &maps, const DenseArgs &a, int grid, cudaStream_t s)
+{
+    const size_t smem = dense_smem(KP);
+    static bool attr_set = false;
+    if (!attr_set) {
+        SME_CUDA(cudaFuncSetAttribute(dense_iteration<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    dense_iteration<KP><<<grid, DN_THREADS, smem, s>>>(maps, a);
+    SME_CUDA(cudaGetLastError());
+    return SME_OK;
+}
+
+static sme_status run_dense(sme_op op, const DenseArgs &a, int buf, cudaStream_t s)
+{
+    DenseOp *D = op->dense;
+    DenseMaps maps;
+    maps.X[0] = D->mapA;
+    maps.X[1] = D->mapAt;
+    maps.B[0] = D->mapBf[buf];
+    maps.B[1] = D->mapBb[buf];
+    const int grid = (int)(D->m / DN_BM + D->n / DN_BM);
+    if (a.kp == 256) return launch_dense<256>(maps, a, grid, s);
+    return launch_dense<128>(maps, a, grid, s);
+}
+
+static DenseArgs dense_base(sme_op op, double alpha, double beta, double gamma, double M, uint64_t seed, int kp)
+{
+    DenseOp *D = op->dense;
+    DenseArgs a{};
+    a.m = D->m;
+    a.n = D->n;
+    a.row_tiles = (int)(D->m / DN_BM);
+    a.kp = kp;
+    a.x[0] = D->x[0];
+    a.x[1] = D->x[1];
+    a.xb[0] = D->xb[0];
+    a.xb[1] = D->xb[1];
+    a.target2[0] = (float)(alpha * alpha);
+    a.target2[1] = (float)(beta * beta);
+    a.gamma = (float)gamma;
+    a.M = (float)M;
+    a.key0 = (uint32_t)seed;
+    a.key1 = (uint32_t)(seed >> 32);
+    a.row_scale = D->row_scale;
+    a.status = op->d_status;
+    return a;
+}
+
+void dense_destroy(sme_op op)
+{
+    DenseOp *D = op->dense;
+    if (!D) return;
+    for (void *p : {(void *)D->A, (void *)D->At, (void *)D->row_scale, (void *)D->Bf[0], (void *)D->Bf[1],
+                    (void *)D->Bb[0], (void *)D->Bb[1], (void *)D->x[0], (void *)D->x[1], (void *)D->xb[0],
+                    (void *)D->xb[1]})
+        if (p) cudaFree(p);
+    delete D;
+    op->dense = nullptr;
+}
+
+static void resolve_params(sme_op op, double &alpha, double &beta, double &gamma, double &M)
+{
+    if (alpha <= 0) alpha = std::pow((double)op->n / (double)op->m, 0.25);
+    if (beta <= 0) beta = std::pow((double)op->m / (double)op->n, 0.25);
+    if (gamma <= 0) gamma = 0.1;
+    if (M <= 0) M = std::log(1e4);
+}
 
 sme_status dense_equilibrate(sme_op op, const sme_equil_params *p, float *u, float *v, float *ub, float *vb,
                              cudaStream_t s)
 {
-    (void)op; (void)p; (void)u; (void)v; (void)ub; (void)vb; (void)s;
-    set_error("dense operators: not built yet");
-    return SME_ERR_UNSUPPORTED;
+    const int kp = p->k;
+    if (kp != 128 && kp != 256) {
+        set_error("dense operators support k = 128 or 256");
+        return SME_ERR_UNSUPPORTED;
+    }
+    SME_TRY(ensure_dense_workspace(op, kp));
+    DenseOp *D = op->dense;
+    double alpha = p->alpha, beta = p->beta, gamma = p->gamma, M = p->M;
+    resolve_params(op, alpha, beta, gamma, M);
+    const uint32_t sid_s = (uint32_t)p->stream_base, sid_w = sid_s + 1u;
+    const int tb = p->t_begin;
+    SME_CUDA(cudaMemcpyAsync(D->x[0], u, D->m * 4, cudaMemcpyDeviceToDevice, s));
+    SME_CUDA(cudaMemcpyAsync(D->xb[0], ub, D->m * 4, cudaMemcpyDeviceToDevice, s));
+    SME_CUDA(cudaMemcpyAsync(D->x[1], v, D->n * 4, cudaMemcpyDeviceToDevice, s));
+    SME_CUDA(cudaMemcpyAsync(D->xb[1], vb, D->n * 4, cudaMemcpyDeviceToDevice, s));
+    const uint32_t k0 = (uint32_t)p->seed, k1 = (uint32_t)(p->seed >> 32);
+    dense_build_operand<<<nblk(D->n), 256, 0, s>>>(D->n, kp, D->x[1], nullptr, (uint32_t)tb, sid_s, k0, k1,
+                                                   D->Bf[tb & 1]);
+    dense_build_operand<<<nblk(D->m), 256, 0, s>>>(D->m, kp, D->x[0], D->row_scale, (uint32_t)tb, sid_w, k0, k1,
+                                                   D->Bb[tb & 1]);
+    SME_CUDA(cudaGetLastError());
+    const bool timed = (p->flags & SME_EQ_TIMED) != 0;
+    if (timed) {
+        for (int i = 0; i < 2; ++i)
+            if (!op->ev_loop[i]) SME_CUDA(cudaEventCreate(&op->ev_loop[i]));
+        SME_CUDA(cudaEventRecord(op->ev_loop[0], s));
+    }
+    for (int t = tb; t < tb + p->T; ++t) {
+        DenseArgs a = dense_base(op, alpha, beta, gamma, M, p->seed, kp);
+        const int cur = t & 1, nxt = cur ^ 1;
+        a.bnext[0] = D->Bb[nxt];
+        a.bnext[1] = D->Bf[nxt];
+        a.eta = (float)(2.0 / (gamma * ((double)t + (double)p->t0 + 1.0)));
+        a.avg_new = (float)(2.0 / ((double)t + 2.0));
+        a.avg_old = (float)((double)t / ((double)t + 2.0));
+        a.t_next = (uint32_t)(t + 1);
+        a.sid_out[0] = sid_w;
+        a.sid_out[1] = sid_s;
+        a.mode = 0;
+        SME_TRY(run_dense(op, a, cur, s));
+    }
+    if (timed) {
+        SME_CUDA(cudaEventRecord(op->ev_loop[1], s));
+        op->loop_timed = true;
+        op->loop_iters = p->T;
+    }
+    SME_CUDA(cudaMemcpyAsync(u, D->x[0], D->m * 4, cudaMemcpyDeviceToDevice, s));
+    SME_CUDA(cudaMemcpyAsync(ub, D->xb[0], D->m * 4, cudaMemcpyDeviceToDevice, s));
+    SME_CUDA(cudaMemcpyAsync(v, D->x[1], D->n * 4, cudaMemcpyDeviceToDevice, s));
+    SME_CUDA(cudaMemcpyAsync(vb, D->xb[1], D->n * 4, cudaMemcpyDeviceToDevice, s));
+    return SME_OK;
 }
 
 sme_status dense_estimate(sme_op op, const float *u, const float *v, int t, int k, uint64_t seed, int sb, float *zu,
                           float *zv, cudaStream_t s)
 {
-    (void)op; (void)u; (void)v; (void)t; (void)k; (void)seed; (void)sb; (void)zu; (void)zv; (void)s;
-    set_error("dense operators: not built yet");
-    return SME_ERR_UNSUPPORTED;
+    if (k != 128 && k != 256) {
+        set_error("dense operators support k = 128 or 256");
+        return SME_ERR_UNSUPPORTED;
+    }
+    SME_TRY(ensure_dense_workspace(op, k));
+    DenseOp *D = op->dense;
+    SME_CUDA(cudaMemcpyAsync(D->x[0], u, D->m * 4, cudaMemcpyDeviceToDevice, s));
+    SME_CUDA(cudaMemcpyAsync(D->x[1], v, D->n * 4, cudaMemcpyDeviceToDevice, s));
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    dense_build_operand<<<nblk(D->n), 256, 0, s>>>(D->n, k, D->x[1], nullptr, (uint32_t)t, (uint32_t)sb, k0, k1,
+                                                   D->Bf[0]);
+    dense_build_operand<<<nblk(D->m), 256, 0, s>>>(D->m, k, D->x[0], D->row_scale, (uint32_t)t, (uint32_t)sb + 1u,
+                                                   k0, k1, D->Bb[0]);
+    double alpha = 0, beta = 0, gamma = 0, M = 0;
+    resolve_params(op, alpha, beta, gamma, M);
+    DenseArgs a = dense_base(op, alpha, beta, gamma, M, seed, k);
+    a.mode = 1;
+    a.z[0] = zu ? zu : D->xb[0];  // a NULL output is written into scratch and ignored
+    a.z[1] = zv ? zv : D->xb[1];
+    return run_dense(op, a, 0, s);
 }
 
 }  // namespace sme
 
+using namespace sme;
+
 extern "C" sme_status sme_op_create_dense(sme_op *out, int64_t m, int64_t n, const void *A, int64_t lda,
                                           sme_dtype dtype, const float *row_scales, int on_device, void *stream)
 {
-    (void)m; (void)n; (void)A; (void)lda; (void)dtype; (void)row_scales; (void)on_device; (void)stream;
-    if (out) *out = nullptr;
-    sme::set_error("sme_op_create_dense: not built yet");
-    return SME_ERR_UNSUPPORTED;
+    if (!out) return SME_ERR_ARG;
+    *out = nullptr;
+    if (m < 128 || n < 128 || m % 128 || n % 128 || !A || lda < n || m > (1 << 30) || n > (1 << 30)) {
+        set_error("sme_op_create_dense: m and n must be positive multiples of 128, lda >= n");
+        return SME_ERR_ARG;
+    }
+    if (dtype != SME_BF16 && dtype != SME_FP8E4M3) {
+        set_error("sme_op_create_dense: dtype must be SME_BF16 or SME_FP8E4M3");
+        return SME_ERR_ARG;
+    }
+    if (dtype == SME_BF16 && row_scales) {
+        set_error("sme_op_create_dense: row_scales apply to SME_FP8E4M3 only");
+        return SME_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    sme_op op = new sme_op_s();
+    op->m = m;
+    op->n = n;
+    op->nnz = m * n;
+    op->dtype = dtype;
+    op->dbl = false;
+    op->dense = new DenseOp();
+    DenseOp *D = op->dense;
+    D->m = m;
+    D->n = n;
+    D->fp8 = dtype == SME_FP8E4M3;
+    sme_status st = SME_OK;
+    auto fail = [&](sme_status e) {
+        sme_op_destroy(op);
+        return e;
+    };
+    if ((st = dev_alloc(op, (void **)&op->d_status, sizeof(int))) != SME_OK) return fail(st);
+    if ((st = dev_alloc(op, (void **)&D->A, (size_t)m * n * 2)) != SME_OK) return fail(st);
+    if ((st = dev_alloc(op, (void **)&D->At, (size_t)m * n * 2)) != SME_OK) return fail(st);
+    if (cudaMemsetAsync(op->d_status, 0, sizeof(int), s) != cudaSuccess) return fail(SME_ERR_CUDA);
+    const size_t esz = D->fp8 ? 1 : 2;
+    const void *src = A;
+    void *staging = nullptr;
+    if (!on_device || lda != n || D->fp8) {
+        // Stage the input densely on the device (copy from host, or repack a strided device matrix).
+        if (cudaMalloc(&staging, (size_t)m * lda * esz) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SME_ERR_OOM);
+        }
+        if (cudaMemcpyAsync(staging, A, (size_t)m * lda * esz, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            s) != cudaSuccess) {
+            cudaFree(staging);
+            return fail(SME_ERR_CUDA);
+        }
+        src = staging;
+    }
+    if (D->fp8) {
+        if (row_scales) {
+            if ((st = dev_alloc(op, (void **)&D->row_scale, (size_t)m * 4)) != SME_OK) {
+                cudaFree(staging);
+                return fail(st);
+            }
+            cudaMemcpyAsync(D->row_scale, row_scales, (size_t)m * 4,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+        }
+        fp8_to_bf16<<<nblk(m * n), 256, 0, s>>>((const uint8_t *)src, m, n, lda, D->A);
+    } else if (lda != n) {
+        cudaMemcpy2DAsync(D->A, (size_t)n * 2, src, (size_t)lda * 2, (size_t)n * 2, (size_t)m, cudaMemcpyDeviceToDevice,
+                          s);
+    } else {
+        cudaMemcpyAsync(D->A, src, (size_t)m * n * 2, cudaMemcpyDeviceToDevice, s);
+    }
+    bf16_check_finite<<<152 * 4, 256, 0, s>>>(D->A, m * n, op->d_status);
+    transpose_bf16<<<dim3((unsigned)(n / 32), (unsigned)(m / 32)), dim3(32, 8), 0, s>>>(D->A, m, n, D->At);
+    int st_h = 0;
+    cudaMemcpyAsync(&st_h, op->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (staging) cudaFree(staging);
+    if (e != cudaSuccess) {
+        cuda_fail(e, "sme_op_create_dense", __LINE__);
+        return fail(SME_ERR_CUDA);
+    }
+    if (st_h & ST_BAD_VALUE) {
+        set_error("sme_op_create_dense: non-finite matrix value");
+        return fail(SME_ERR_NONFINITE);
+    }
+    if ((st = make_map(&D->mapA, D->A, m, n, DN_BM)) != SME_OK) return fail(st);
+    if ((st = make_map(&D->mapAt, D->At, n, m, DN_BM)) != SME_OK) return fail(st);
+    *out = op;
+    return SME_OK;
 }

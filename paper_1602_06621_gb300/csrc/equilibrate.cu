@@ -523,7 +523,7 @@ extern "C" sme_status sme_equilibrate(sme_op op, const sme_equil_params *p, void
         set_error("sme_equilibrate: bad arguments");
         return SME_ERR_ARG;
     }
-    if (!k_supported(p->k)) {
+    if (!op->dense && !k_supported(p->k)) {
         set_error("sme_equilibrate: k=%d not supported (1,2,4,...,64)", p->k);
         return SME_ERR_UNSUPPORTED;
     }
@@ -548,7 +548,7 @@ extern "C" sme_status sme_estimate(sme_op op, const void *u, const void *v, int3
         set_error("sme_estimate: bad arguments");
         return SME_ERR_ARG;
     }
-    if (!k_supported(k)) {
+    if (!op->dense && !k_supported(k)) {
         set_error("sme_estimate: k=%d not supported", k);
         return SME_ERR_UNSUPPORTED;
     }

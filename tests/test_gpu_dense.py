@@ -1,0 +1,174 @@
+"""GPU parity of the dense tensor-core path (BF16 and FP8-E4M3 operands, FP32 accumulation).
+
+The oracle sees the same matrix the tensor cores see (the BF16- or E4M3-rounded values, widened to
+FP64), so what is measured is the arithmetic of the path: the two-term BF16 split of the scalings
+(relative error <= 2^-16 per scaling) and FP32 accumulation over K terms.  Bound used:
+|dz_i| <= 2e-5 r2_i with r2_i the exact squared norm of row i of DAE.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1602_06621_gb300 import inputs as I
+from paper_1602_06621_gb300 import sme
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16_matrix(m, n, seed):
+    import torch
+    A = torch.tensor(I.dense_badly_scaled(m, n, seed), dtype=torch.float32)
+    Ab = A.to(torch.bfloat16)
+    return Ab.cuda(), Ab.float().numpy()
+
+
+def _exact_sq(Af, u, v, row_scale=None):
+    B = np.exp(u)[:, None] * Af.astype(np.float64) * np.exp(v)[None, :]
+    if row_scale is not None:
+        B = B * np.asarray(row_scale, np.float64)[:, None]
+    return (B ** 2).sum(1), (B ** 2).sum(0)
+
+
+def _gpu_estimate(op, m, n, u, v, t, k, seed):
+    import torch
+    zu = torch.full((m,), float("nan"), device="cuda")
+    zv = torch.full((n,), float("nan"), device="cuda")
+    sme.sme_estimate(op, torch.tensor(u, dtype=torch.float32, device="cuda"),
+                     torch.tensor(v, dtype=torch.float32, device="cuda"), t, k, seed, 0, zu, zv)
+    torch.cuda.synchronize()
+    return zu.cpu().double().numpy(), zv.cpu().double().numpy()
+
+
+@pytest.mark.parametrize("m,n", [(256, 256), (384, 256), (256, 512)])
+@pytest.mark.parametrize("k", [128, 256])
+def test_dense_estimate_matches_oracle(m, n, k):
+    Ad, Af = _bf16_matrix(m, n, seed=m + n + k)
+    op = sme.sme_op_create_dense(m, n, Ad, dtype=sme.SME_BF16)
+    try:
+        rng = np.random.default_rng(k)
+        u = rng.normal(0, 0.5, m).astype(np.float32)
+        v = rng.normal(0, 0.5, n).astype(np.float32)
+        zu, zv = _gpu_estimate(op, m, n, u, v, t=3, k=k, seed=7)
+    finally:
+        sme.sme_op_destroy(op)
+    ezu, ezv = O.dense_estimate_sampled(Af, u, v, np.arange(m), np.arange(n), t=3, k=k, seed=7)
+    r2, c2 = _exact_sq(Af, u.astype(np.float64), v.astype(np.float64))
+    assert np.all(np.abs(zu - ezu) <= 2e-5 * r2), np.max(np.abs(zu - ezu) / r2)
+    assert np.all(np.abs(zv - ezv) <= 2e-5 * c2), np.max(np.abs(zv - ezv) / c2)
+
+
+def test_dense_every_step_matches_oracle():
+    """20 iterations of Algorithm 1 on a 256 x 384 dense matrix, k = 256, each step checked against the
+    oracle's step from the GPU's own state (norm-wise relative error of [u; v; ubar; vbar] <= 1e-4)."""
+    import torch
+    m, n, k = 256, 384, 256
+    Ad, Af = _bf16_matrix(m, n, seed=5)
+    A64 = O.OracleCSR.from_any(Af.astype(np.float64))
+    d = O.default_params(m, n)
+    op = sme.sme_op_create_dense(m, n, Ad, dtype=sme.SME_BF16)
+    worst = 0.0
+    state = (np.zeros(m), np.zeros(n), np.zeros(m), np.zeros(n))
+    try:
+        for t in range(1, 21):
+            g = [torch.tensor(x, dtype=torch.float32, device="cuda") for x in state]
+            sme.sme_equilibrate(op, *g, T=1, k=k, seed=3, t_begin=t)
+            got = [x.cpu().double().numpy() for x in g]
+            ref = O.psgd_step(A64, *state, O.probe_signs(3, t, 0, n, k), O.probe_signs(3, t, 1, m, k), t, **d)
+            a = np.concatenate(got)
+            b = np.concatenate(ref)
+            worst = max(worst, np.linalg.norm(a - b) / np.linalg.norm(b))
+            state = tuple(got)
+        # One 20-iteration call equals the step-by-step run (resume is exact on the dense path too).
+        g = [torch.zeros(x, device="cuda") for x in (m, n, m, n)]
+        sme.sme_equilibrate(op, *g, T=20, k=k, seed=3)
+        for x, y in zip(g, state):
+            np.testing.assert_array_equal(x.cpu().double().numpy(), y)
+    finally:
+        sme.sme_op_destroy(op)
+    assert worst <= 1e-4, worst
+
+
+def _e4m3_values():
+    """The 256 E4M3 code points (1 sign, 4 exponent bits with bias 7, 3 mantissa bits; codes 0x7f and 0xff
+    are NaN, there is no infinity)."""
+    vals = np.zeros(256)
+    for b in range(256):
+        s, e, f = b >> 7, (b >> 3) & 15, b & 7
+        if (b & 0x7F) == 0x7F:
+            vals[b] = np.nan
+            continue
+        v = f * 2.0 ** -9 if e == 0 else (8 + f) * 2.0 ** (e - 10)
+        vals[b] = -v if s else v
+    return vals
+
+
+def test_dense_fp8_with_row_scales_matches_oracle():
+    import torch
+    m, n, k = 256, 256, 256
+    rng = np.random.default_rng(11)
+    codes = rng.integers(0, 256, size=(m, n)).astype(np.uint8)
+    codes[(codes & 0x7F) == 0x7F] = 0x38  # no NaN codes (0x38 is 1.0)
+    scales = np.exp(rng.normal(0, 1.5, m)).astype(np.float32)
+    table = _e4m3_values()
+    Af = table[codes].astype(np.float32)  # exact
+    op = sme.sme_op_create_dense(m, n, torch.tensor(codes, device="cuda"), dtype=sme.SME_FP8E4M3,
+                                 row_scales=torch.tensor(scales, device="cuda"))
+    try:
+        u = rng.normal(0, 0.5, m).astype(np.float32)
+        v = rng.normal(0, 0.5, n).astype(np.float32)
+        zu, zv = _gpu_estimate(op, m, n, u, v, t=2, k=k, seed=9)
+    finally:
+        sme.sme_op_destroy(op)
+    ezu, ezv = O.dense_estimate_sampled(Af, u, v, np.arange(m), np.arange(n), t=2, k=k, seed=9, row_scale=scales)
+    r2, c2 = _exact_sq(Af, u.astype(np.float64), v.astype(np.float64), row_scale=scales)
+    assert np.all(np.abs(zu - ezu) <= 2e-5 * r2)
+    assert np.all(np.abs(zv - ezv) <= 2e-5 * c2)
+
+
+def test_dense_full_size_sampled_estimate():
+    """16384 x 16384 BF16 (entries N(0,1) e^{r_i + c_j}, factors of variance 1.5), k = 256: sampled rows and
+    columns of one estimate against the oracle."""
+    import torch
+    m = n = 16384
+    A32 = I.dense_badly_scaled(m, n, seed=3)
+    Ad = torch.from_numpy(A32).to(torch.bfloat16).cuda()
+    Af = Ad.float().cpu().numpy()
+    del A32
+    op = sme.sme_op_create_dense(m, n, Ad, dtype=sme.SME_BF16)
+    try:
+        rng = np.random.default_rng(0)
+        u = rng.normal(0, 0.5, m).astype(np.float32)
+        v = rng.normal(0, 0.5, n).astype(np.float32)
+        zu, zv = _gpu_estimate(op, m, n, u, v, t=1, k=256, seed=0)
+    finally:
+        sme.sme_op_destroy(op)
+    rows = np.sort(rng.choice(m, 24, replace=False))
+    cols = np.sort(rng.choice(n, 24, replace=False))
+    ezu, ezv = O.dense_estimate_sampled(Af, u, v, rows, cols, t=1, k=256, seed=0)
+    u64, v64 = u.astype(np.float64), v.astype(np.float64)
+    r2 = np.array([np.sum((np.exp(u64[i]) * Af[i].astype(np.float64) * np.exp(v64)) ** 2) for i in rows])
+    c2 = np.array([np.sum((np.exp(u64) * Af[:, j].astype(np.float64) * np.exp(v64[j])) ** 2) for j in cols])
+    assert np.all(np.abs(zu[rows] - ezu) <= 2e-5 * r2)
+    assert np.all(np.abs(zv[cols] - ezv) <= 2e-5 * c2)
+    assert np.all(np.isfinite(zu)) and np.all(np.isfinite(zv))
+
+
+def test_dense_argument_errors():
+    import torch
+    A = torch.zeros((200, 256), dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(sme.SmeError) as ei:
+        sme.sme_op_create_dense(200, 256, A, dtype=sme.SME_BF16)
+    assert ei.value.name == "SME_ERR_ARG"
+    A = torch.zeros((256, 256), dtype=torch.bfloat16, device="cuda")
+    op = sme.sme_op_create_dense(256, 256, A, dtype=sme.SME_BF16)
+    try:
+        z = torch.zeros(256, device="cuda")
+        with pytest.raises(sme.SmeError) as ei:
+            sme.sme_equilibrate(op, z, z.clone(), z.clone(), z.clone(), T=1, k=32)
+        assert ei.value.name == "SME_ERR_UNSUPPORTED"
+    finally:
+        sme.sme_op_destroy(op)
+    A[3, 4] = float("nan")
+    with pytest.raises(sme.SmeError) as ei:
+        sme.sme_op_create_dense(256, 256, A, dtype=sme.SME_BF16)
+    assert ei.value.name == "SME_ERR_NONFINITE"
