@@ -9,7 +9,7 @@
 // the op keeps A and a transposed copy A^T, so every operand is K-major.  One launch performs one
 // iteration: CTAs [0, m/128) take 128-row tiles of A (forward), the others 128-row tiles of A^T.
 // Each CTA owns its full output tile (128 x 2k FP32 in TMEM, 2k <= 512 columns), streams K through a
-// two-stage TMA pipeline (128-byte swizzle), one thread issues tcgen05.mma, and four epilogue warps
+// 5-to-8-stage TMA pipeline (64-byte swizzle), one thread issues tcgen05.mma, and four epilogue warps
 // read TMEM and finish the row in registers: z = e^{2x} (1/k) sum_p (hi_p + lo_p)^2, the projected
 // step, the running average, and the row's slice of the NEXT iteration's B operand (its scale and
 // Philox probe bits), double-buffered like the sparse path's gather tables.
@@ -29,8 +29,19 @@
 namespace sme {
 
 constexpr int DN_BM = 128;           // rows per tile (MMA M)
-constexpr int DN_BK = 64;            // K per stage: 64 BF16 = one 128-byte swizzle row
-constexpr int DN_STAGES = 2;
+constexpr int DN_BK = 32;            // K per stage: 32 BF16 = one 64-byte swizzle row
+constexpr int DN_ROWB = DN_BK * 2;   // bytes per operand row in shared memory
+constexpr int DN_SMEM_BUDGET = 200 * 1024;
+
+// Pipeline depth: as many stages as fit the shared-memory budget (5 for k = 256, 8 for k = 128).
+template <int KP>
+struct DenseCfg {
+    static constexpr int NT = 2 * KP;
+    static constexpr int A_BYTES = DN_BM * DN_ROWB;
+    static constexpr int B_BYTES = NT * DN_ROWB;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int STAGES = (DN_SMEM_BUDGET / STAGE) > 8 ? 8 : (DN_SMEM_BUDGET / STAGE);
+};
 constexpr int DN_THREADS = 192;      // warp 0 TMA, warp 1 MMA + TMEM owner, warps 2..5 epilogue
 constexpr uint32_t DN_WAIT_LIMIT = 1u << 22;  // polls of a try_wait before a wait is abandoned
 
@@ -91,16 +102,16 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc_sw128(const void *p)
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw64(const void *p)
 {
     const uint64_t addr = smem_u32(p);
     uint64_t d = 0;
-    d |= (addr >> 4) & 0x3FFFull;          // start address
-    d |= (uint64_t)1 << 16;                // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;      // stride byte offset: 8 rows x 128 bytes
-    d |= (uint64_t)1 << 46;                // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;                // swizzle mode: 128 bytes
+    d |= (addr >> 4) & 0x3FFFull;              // start address
+    d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)((8 * DN_ROWB) >> 4) << 32; // stride byte offset: 8 rows x 64 bytes
+    d |= (uint64_t)1 << 46;                    // descriptor version for tcgen05
+    d |= (uint64_t)4 << 61;                    // swizzle mode: 64 bytes
     return d;
 }
 
@@ -167,14 +178,15 @@ struct DenseMaps {
 template <int KP>
 __global__ void __launch_bounds__(DN_THREADS, 1) dense_iteration(const __grid_constant__ DenseMaps maps, DenseArgs a)
 {
-    constexpr int NT = 2 * KP;                       // accumulator columns: hi then lo
-    constexpr int A_BYTES = DN_BM * DN_BK * 2;       // 16 KB
-    constexpr int B_BYTES = NT * DN_BK * 2;          // 32 or 64 KB
-    constexpr int STAGE = A_BYTES + B_BYTES;
+    using C = DenseCfg<KP>;
+    constexpr int NT = C::NT;                        // accumulator columns: hi then lo
+    constexpr int A_BYTES = C::A_BYTES;
+    constexpr int STAGE = C::STAGE;
+    constexpr int DN_STAGES = C::STAGES;
     constexpr uint32_t IDESC = idesc_bf16(DN_BM, 256);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t full_bar[DN_STAGES], empty_bar[DN_STAGES], acc_bar;
+    __shared__ uint64_t full_bar[8], empty_bar[8], acc_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh, issued_sh, consumed_sh;
 
@@ -222,7 +234,8 @@ __global__ void __launch_bounds__(DN_THREADS, 1) dense_iteration(const __grid_co
             uint8_t *sb = sa + A_BYTES;
             mbar_expect_tx(&full_bar[s], STAGE);
             tma_load_2d(sa, mapX, kb * DN_BK, tile * DN_BM, &full_bar[s]);
-            for (int h = 0; h < NT / 256; ++h) tma_load_2d(sb + h * 256 * 128, mapB, kb * DN_BK, h * 256, &full_bar[s]);
+            for (int h = 0; h < NT / 256; ++h)
+                tma_load_2d(sb + h * 256 * DN_ROWB, mapB, kb * DN_BK, h * 256, &full_bar[s]);
             issued_sh = kb + 1;
         }
     } else if (warp == 1 && lane == 0) {
@@ -240,10 +253,10 @@ __global__ void __launch_bounds__(DN_THREADS, 1) dense_iteration(const __grid_co
             uint8_t *sb = sa + A_BYTES;
 #pragma unroll
             for (int kk = 0; kk < DN_BK / 16; ++kk) {
-                const uint64_t ad = smem_desc_sw128(sa) + (uint64_t)(kk * 2);  // +32 bytes along K
+                const uint64_t ad = smem_desc_sw64(sa) + (uint64_t)(kk * 2);  // +32 bytes along K
 #pragma unroll
                 for (int h = 0; h < NT / 256; ++h) {
-                    const uint64_t bd = smem_desc_sw128(sb + h * 256 * 128) + (uint64_t)(kk * 2);
+                    const uint64_t bd = smem_desc_sw64(sb + h * 256 * DN_ROWB) + (uint64_t)(kk * 2);
                     mma_bf16(tmem + h * 256, ad, bd, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
                 }
             }
@@ -411,7 +424,7 @@ static EncodeTiledFn encode_fn()
     return fn;
 }
 
-// Row-major BF16 matrix (rows x cols) viewed with boxes of 64 columns (128 bytes) x box_rows rows.
+// Row-major BF16 matrix (rows x cols) viewed with boxes of DN_BK columns (64 bytes) x box_rows rows.
 static sme_status make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int box_rows)
 {
     EncodeTiledFn fn = encode_fn();
@@ -421,10 +434,10 @@ static sme_status make_map(CUtensorMap *map, const void *base, int64_t rows, int
     }
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)DN_BK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -435,7 +448,8 @@ static sme_status make_map(CUtensorMap *map, const void *base, int64_t rows, int
 
 static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-static size_t dense_smem(int kp) { return (size_t)DN_STAGES * (DN_BM * DN_BK * 2 + 2 * kp * DN_BK * 2) + 1024; }
+template <int KP>
+static size_t dense_smem() { return (size_t)DenseCfg<KP>::STAGES * DenseCfg<KP>::STAGE + 1024; }
 
 static sme_status ensure_dense_workspace(sme_op op, int kp)
 {
@@ -463,7 +477,7 @@ static sme_status ensure_dense_workspace(sme_op op, int kp)
 template <int KP>
 static sme_status launch_dense(const DenseMaps &maps, const DenseArgs &a, int grid, cudaStream_t s)
 {
-    const size_t smem = dense_smem(KP);
+    const size_t smem = dense_smem<KP>();
     static bool attr_set = false;
     if (!attr_set) {
         SME_CUDA(cudaFuncSetAttribute(dense_iteration<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -1,9 +1,14 @@
 """GPU parity of the dense tensor-core path (BF16 and FP8-E4M3 operands, FP32 accumulation).
 
 The oracle sees the same matrix the tensor cores see (the BF16- or E4M3-rounded values, widened to
-FP64), so what is measured is the arithmetic of the path: the two-term BF16 split of the scalings
-(relative error <= 2^-16 per scaling) and FP32 accumulation over K terms.  Bound used:
-|dz_i| <= 2e-5 r2_i with r2_i the exact squared norm of row i of DAE.
+FP64), so what is measured is the arithmetic of the path:
+  * the two-term BF16 split of the scalings (relative error <= 2^-17 per scaling), and
+  * FP32 accumulation in the tensor cores, which aligns and truncates (rounds toward zero) when it adds
+    each block of products to the accumulator, so its error is one-sided and grows with the number of
+    16-term MMAs, K/16: on average about 2^-24 of the accumulator per MMA.
+Bound used: |dz_i| <= (2e-5 + (K/16) 2^-24) r2_i, with r2_i the exact squared norm of row i of DAE and K the
+reduction length (n for rows, m for columns).  At K = 16384 that is 8.1e-5; the measured error there is
+about 3e-5, biased low.
 """
 import numpy as np
 import pytest
@@ -27,6 +32,10 @@ def _exact_sq(Af, u, v, row_scale=None):
     if row_scale is not None:
         B = B * np.asarray(row_scale, np.float64)[:, None]
     return (B ** 2).sum(1), (B ** 2).sum(0)
+
+
+def _tol(K):
+    return 2e-5 + (K / 16) * 2.0 ** -24
 
 
 def _gpu_estimate(op, m, n, u, v, t, k, seed):
@@ -53,8 +62,8 @@ def test_dense_estimate_matches_oracle(m, n, k):
         sme.sme_op_destroy(op)
     ezu, ezv = O.dense_estimate_sampled(Af, u, v, np.arange(m), np.arange(n), t=3, k=k, seed=7)
     r2, c2 = _exact_sq(Af, u.astype(np.float64), v.astype(np.float64))
-    assert np.all(np.abs(zu - ezu) <= 2e-5 * r2), np.max(np.abs(zu - ezu) / r2)
-    assert np.all(np.abs(zv - ezv) <= 2e-5 * c2), np.max(np.abs(zv - ezv) / c2)
+    assert np.all(np.abs(zu - ezu) <= _tol(n) * r2), np.max(np.abs(zu - ezu) / r2)
+    assert np.all(np.abs(zv - ezv) <= _tol(m) * c2), np.max(np.abs(zv - ezv) / c2)
 
 
 def test_dense_every_step_matches_oracle():
@@ -121,8 +130,8 @@ def test_dense_fp8_with_row_scales_matches_oracle():
         sme.sme_op_destroy(op)
     ezu, ezv = O.dense_estimate_sampled(Af, u, v, np.arange(m), np.arange(n), t=2, k=k, seed=9, row_scale=scales)
     r2, c2 = _exact_sq(Af, u.astype(np.float64), v.astype(np.float64), row_scale=scales)
-    assert np.all(np.abs(zu - ezu) <= 2e-5 * r2)
-    assert np.all(np.abs(zv - ezv) <= 2e-5 * c2)
+    assert np.all(np.abs(zu - ezu) <= _tol(n) * r2)
+    assert np.all(np.abs(zv - ezv) <= _tol(m) * c2)
 
 
 def test_dense_full_size_sampled_estimate():
@@ -148,8 +157,8 @@ def test_dense_full_size_sampled_estimate():
     u64, v64 = u.astype(np.float64), v.astype(np.float64)
     r2 = np.array([np.sum((np.exp(u64[i]) * Af[i].astype(np.float64) * np.exp(v64)) ** 2) for i in rows])
     c2 = np.array([np.sum((np.exp(u64) * Af[:, j].astype(np.float64) * np.exp(v64[j])) ** 2) for j in cols])
-    assert np.all(np.abs(zu[rows] - ezu) <= 2e-5 * r2)
-    assert np.all(np.abs(zv[cols] - ezv) <= 2e-5 * c2)
+    assert np.all(np.abs(zu[rows] - ezu) <= _tol(n) * r2), np.max(np.abs(zu[rows] - ezu) / r2)
+    assert np.all(np.abs(zv[cols] - ezv) <= _tol(m) * c2), np.max(np.abs(zv[cols] - ezv) / c2)
     assert np.all(np.isfinite(zu)) and np.all(np.isfinite(zv))
 
 
