@@ -215,6 +215,49 @@ typedef struct {
 sme_status sme_lsqr(sme_op op, const void *u_bar, const void *v_bar, const void *b, void *x,
                     const sme_lsqr_params *p, sme_lsqr_result *res, void *stream);
 
+/* ------------------------------------------------------------------ batches */
+
+/*
+ * A batch of sparse matrices equilibrated together (Algorithm 1 run on each matrix, all matrices
+ * advanced by the same launches).  The batch is one block-diagonal operator diag(A_0, ..., A_{B-1})
+ * whose rows and columns are sorted by length across the whole batch, so matrices of very different
+ * sizes share the same work units.  Matrix b draws its probes from Philox streams stream_base + 2b (s)
+ * and stream_base + 2b + 1 (w) with counters indexed inside matrix b, so its result equals a separate
+ * sme_equilibrate of A_b with stream_base + 2b, bit for bit.
+ */
+typedef struct sme_batch_s *sme_batch;
+
+/*
+ * sme_batch_create -- count matrices in CSR, HOST arrays: m[b], n[b], row_ptr[b] (int32[m[b]+1]),
+ * col_idx[b], vals[b] (dtype SME_F32 or SME_F64), each validated as in sme_op_create_csr.  The totals of
+ * rows, columns and nonzeros must stay below 2^31.  Synchronises `stream`.
+ */
+sme_status sme_batch_create(sme_batch *out, int32_t count, const int64_t *m, const int64_t *n,
+                            const int32_t *const *row_ptr, const int32_t *const *col_idx, const void *const *vals,
+                            sme_dtype dtype, void *stream);
+sme_status sme_batch_destroy(sme_batch b);
+
+/* Number of matrices and the offsets of matrix b's rows [row_off[b], row_off[b+1]) and columns in the
+ * concatenated vectors (host arrays of count + 1 entries, either may be NULL). */
+sme_status sme_batch_get_info(sme_batch b, int32_t *count, int64_t *row_off, int64_t *col_off);
+
+/*
+ * sme_batch_equilibrate -- sme_equilibrate for every matrix of the batch at once.  u, u_bar are the
+ * concatenated row vectors (sum of m[b] entries, matrix order), v, v_bar the concatenated column
+ * vectors.  alpha, beta <= 0 select each matrix's own (n_b/m_b)^(1/4), (m_b/n_b)^(1/4); gamma, M, T, k,
+ * t_begin, t0, seed, flags apply to all.  Unless SME_EQ_ASYNC, synchronises and checks the status word.
+ */
+sme_status sme_batch_equilibrate(sme_batch b, const sme_equil_params *p, void *u, void *v, void *u_bar,
+                                 void *v_bar, void *stream);
+
+/* sme_estimate for every matrix of the batch (concatenated vectors; probes as in sme_batch_equilibrate). */
+sme_status sme_batch_estimate(sme_batch b, const void *u, const void *v, int32_t t, int32_t k, uint64_t seed,
+                              int32_t stream_base, void *z_u, void *z_v, void *stream);
+
+/* The block-diagonal operator of the batch (owned by the batch; do not destroy it), for sme_evaluate
+ * of all matrices at once (row / column norms come back concatenated). */
+sme_status sme_batch_op(sme_batch b, sme_op *op);
+
 /* ------------------------------------------------------------------ allocation-free estimator */
 
 /*

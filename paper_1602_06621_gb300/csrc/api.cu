@@ -90,6 +90,13 @@ static sme_status validate_host(int64_t m, int64_t n, int64_t nnz, const int32_t
     return SME_OK;
 }
 
+sme_status validate_csr_host(int64_t m, int64_t n, int64_t nnz, const int32_t *rp, const int32_t *col,
+                             const void *vals, sme_dtype dtype)
+{
+    return dtype == SME_F64 ? validate_host<double>(m, n, nnz, rp, col, (const double *)vals)
+                            : validate_host<float>(m, n, nnz, rp, col, (const float *)vals);
+}
+
 }  // namespace sme
 
 using namespace sme;
@@ -123,7 +130,16 @@ extern "C" sme_status sme_op_destroy(sme_op op)
         if (p) cudaFree(p);
     release_lsqr(op);
     if (op->graph.exec) cudaGraphExecDestroy(op->graph.exec);
+    if (op->graph.stream) cudaStreamDestroy(op->graph.stream);
     if (op->dense) dense_destroy(op);
+    if (op->batch) {
+        for (int side = 0; side < 2; ++side)
+            for (void *p : {(void *)op->batch->mid[side], (void *)op->batch->loc[side], op->batch->tgt2[side]})
+                if (p) cudaFree(p);
+        delete[] op->batch->row_off;
+        delete[] op->batch->col_off;
+        delete op->batch;
+    }
     if (op->d_status) cudaFree(op->d_status);
     for (cudaEvent_t e : op->ev_loop)
         if (e) cudaEventDestroy(e);

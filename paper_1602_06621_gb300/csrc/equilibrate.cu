@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "sme_internal.cuh"
 
@@ -48,6 +49,12 @@ struct StepArgs {
     int64_t blocks0;
     int mode;               // 0: full step, 1: estimate only
     int *status;
+    // Batches of matrices (block-diagonal operator): per sorted row / column the matrix id and the
+    // index inside that matrix, per matrix the squared targets; null for a single matrix.
+    const int32_t *mid[2];
+    const int32_t *loc[2];
+    const real *tgt2[2];
+    uint32_t sid_base;
 };
 
 // ------------------------------------------------------------------ gather tables
@@ -265,21 +272,32 @@ __global__ void __launch_bounds__(ITER_THREADS) sgd_iteration(StepArgs<real> a)
         (cols ? a.z[1] : a.z[0])[S.perm[r]] = z;
         return;
     }
-    real xn = xo - a.eta * (z - (cols ? a.target2[1] : a.target2[0]) + a.gamma * xo);
+    const int32_t *MID = cols ? a.mid[1] : a.mid[0];
+    real t2 = cols ? a.target2[1] : a.target2[0];
+    uint32_t pidx = (uint32_t)S.perm[r];
+    uint32_t psid = cols ? a.sid_out[1] : a.sid_out[0];
+    if (MID) {
+        const int32_t b = MID[r];
+        t2 = (cols ? a.tgt2[1] : a.tgt2[0])[b];
+        pidx = (uint32_t)(cols ? a.loc[1] : a.loc[0])[r];
+        psid = a.sid_base + 2u * (uint32_t)b + (cols ? 0u : 1u);
+    }
+    real xn = xo - a.eta * (z - t2 + a.gamma * xo);
     if (!isfinite(xn)) atomicOr(a.status, ST_NONFINITE);
     xn = dclip(xn, a.M);
     X[r] = xn;
     real *XB = cols ? a.xb[1] : a.xb[0];
     XB[r] = a.avg_new * xn + a.avg_old * XB[r];
     uint32_t pw0, pw1;
-    probe_words2((uint32_t)S.perm[r], a.t_next, cols ? a.sid_out[1] : a.sid_out[0], a.key0, a.key1, pw0, pw1);
+    probe_words2(pidx, a.t_next, psid, a.key0, a.key1, pw0, pw1);
     Tab::store(cols ? a.tab_out[1] : a.tab_out[0], r, dexp(xn), pw0, pw1);
 }
 
 // Load a start state (original order) into sorted order and build the tables of iteration t.
 template <typename real, int KW>
 __global__ void load_state(int64_t rows, const int32_t *perm, const real *x_in, const real *xb_in, real *x,
-                           real *xb, void *tab, uint32_t t, uint32_t sid, uint32_t k0, uint32_t k1)
+                           real *xb, void *tab, uint32_t t, uint32_t sid, uint32_t k0, uint32_t k1,
+                           const int32_t *mid, const int32_t *loc, uint32_t sid_base, uint32_t side_off)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rows) return;
@@ -287,8 +305,13 @@ __global__ void load_state(int64_t rows, const int32_t *perm, const real *x_in, 
     const real xi = x_in ? x_in[i] : real(0);
     if (x) x[r] = xi;
     if (xb) xb[r] = xb_in ? xb_in[i] : real(0);
+    uint32_t pidx = (uint32_t)i, psid = sid;
+    if (mid) {
+        pidx = (uint32_t)loc[r];
+        psid = sid_base + 2u * (uint32_t)mid[r] + side_off;
+    }
     uint32_t w0, w1;
-    probe_words2((uint32_t)i, t, sid, k0, k1, w0, w1);
+    probe_words2(pidx, t, psid, k0, k1, w0, w1);
     TabEntry<real, KW>::store(tab, r, dexp(xi), w0, w1);
 }
 
@@ -320,6 +343,8 @@ __global__ void draw_probe_words(uint64_t seed, uint32_t t, uint32_t sid, int64_
 static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 static bool k_supported(int k) { return k == 1 || k == 2 || k == 4 || k == 8 || k == 16 || k == 32 || k == 64; }
+
+bool probes_supported(int k) { return k_supported(k); }
 
 static int entry_bytes(bool dbl, int kw) { return (!dbl && kw == 1) ? 8 : 16; }
 
@@ -376,14 +401,20 @@ static void launch_iteration(const StepArgs<real> &a, int k, unsigned grid, cuda
 
 template <typename real>
 static void launch_load(sme_op op, int side, int kw, const real *x_in, const real *xb_in, real *x, real *xb,
-                        void *tab, uint32_t t, uint32_t sid, uint64_t seed, cudaStream_t s)
+                        void *tab, uint32_t t, uint32_t sid, uint64_t seed, cudaStream_t s, uint32_t sid_base = 0)
 {
     const Sell &S = side == 0 ? op->fwd : op->bwd;
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    const int32_t *mid = op->batch ? op->batch->mid[side] : nullptr;
+    const int32_t *loc = op->batch ? op->batch->loc[side] : nullptr;
+    if (op->batch) sid_base = op->batch->sid_base;
+    const uint32_t side_off = side == 0 ? 1u : 0u;
     if (op->dbl || kw == 2)
-        load_state<real, 2><<<nblk(S.rows), 256, 0, s>>>(S.rows, S.perm, x_in, xb_in, x, xb, tab, t, sid, k0, k1);
+        load_state<real, 2><<<nblk(S.rows), 256, 0, s>>>(S.rows, S.perm, x_in, xb_in, x, xb, tab, t, sid, k0, k1, mid,
+                                                         loc, sid_base, side_off);
     else
-        load_state<real, 1><<<nblk(S.rows), 256, 0, s>>>(S.rows, S.perm, x_in, xb_in, x, xb, tab, t, sid, k0, k1);
+        load_state<real, 1><<<nblk(S.rows), 256, 0, s>>>(S.rows, S.perm, x_in, xb_in, x, xb, tab, t, sid, k0, k1, mid,
+                                                         loc, sid_base, side_off);
 }
 
 struct Resolved {
@@ -422,6 +453,14 @@ static StepArgs<real> base_args(sme_op op, int buf_in, const Resolved &R, uint64
     a.key1 = (uint32_t)(seed >> 32);
     a.blocks0 = (op->fwd.nslices + SLICES_PER_CTA - 1) / SLICES_PER_CTA;
     a.status = op->d_status;
+    if (op->batch) {
+        for (int side = 0; side < 2; ++side) {
+            a.mid[side] = op->batch->mid[side];
+            a.loc[side] = op->batch->loc[side];
+            a.tgt2[side] = (const real *)op->batch->tgt2[side];
+        }
+        a.sid_base = op->batch->sid_base;
+    }
     return a;
 }
 
@@ -438,6 +477,7 @@ static sme_status equilibrate_t(sme_op op, const sme_equil_params *p, real *u, r
     const int k = p->k, kw = (k + 31) / 32;
     SME_TRY(ensure_equil_workspace(op, kw));
     const Resolved R = resolve(op, p->alpha, p->beta, p->gamma, p->M);
+    if (op->batch) op->batch->sid_base = (uint32_t)p->stream_base;
     const uint32_t sid_s = (uint32_t)p->stream_base, sid_w = (uint32_t)p->stream_base + 1u;
     const int tb = p->t_begin;
     int buf = tb & 1;
@@ -452,16 +492,44 @@ static sme_status equilibrate_t(sme_op op, const sme_equil_params *p, real *u, r
             if (!op->ev_loop[i]) SME_CUDA(cudaEventCreate(&op->ev_loop[i]));
         SME_CUDA(cudaEventRecord(op->ev_loop[0], s));
     }
-    for (int t = tb; t < tb + p->T; ++t) {
-        StepArgs<real> a = base_args<real>(op, t & 1, R, p->seed);
-        a.eta = (real)(2.0 / (R.gamma * ((double)t + (double)p->t0 + 1.0)));
-        a.avg_new = (real)(2.0 / ((double)t + 2.0));
-        a.avg_old = (real)((double)t / ((double)t + 2.0));
-        a.t_next = (uint32_t)(t + 1);
-        a.sid_out[0] = sid_w;
-        a.sid_out[1] = sid_s;
-        a.mode = 0;
-        launch_iteration<real>(a, k, grid, s);
+    auto enqueue = [&](cudaStream_t q) {
+        for (int t = tb; t < tb + p->T; ++t) {
+            StepArgs<real> a = base_args<real>(op, t & 1, R, p->seed);
+            a.eta = (real)(2.0 / (R.gamma * ((double)t + (double)p->t0 + 1.0)));
+            a.avg_new = (real)(2.0 / ((double)t + 2.0));
+            a.avg_old = (real)((double)t / ((double)t + 2.0));
+            a.t_next = (uint32_t)(t + 1);
+            a.sid_out[0] = sid_w;
+            a.sid_out[1] = sid_s;
+            a.mode = 0;
+            launch_iteration<real>(a, k, grid, q);
+        }
+    };
+    if ((p->flags & SME_EQ_NO_GRAPH) || p->T < 2) {
+        enqueue(s);
+    } else {
+        // The iteration launches depend only on these values (all buffers they touch belong to the op),
+        // so one captured graph is replayed for repeated calls with the same parameters.
+        const int64_t key[12] = {p->T, p->k, p->t_begin, p->t0, (int64_t)p->seed, p->stream_base,
+                                 (int64_t)(R.alpha * 1e15), (int64_t)(R.beta * 1e15), (int64_t)(R.gamma * 1e15),
+                                 (int64_t)(R.M * 1e15), (int64_t)op->ws.tab_bytes_u, 1};
+        GraphCache &G = op->graph;
+        if (!G.exec || std::memcmp(G.key, key, sizeof(key)) != 0) {
+            if (G.exec) {
+                cudaGraphExecDestroy(G.exec);
+                G.exec = nullptr;
+            }
+            if (!G.stream) SME_CUDA(cudaStreamCreateWithFlags(&G.stream, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            SME_CUDA(cudaStreamBeginCapture(G.stream, cudaStreamCaptureModeThreadLocal));
+            enqueue(G.stream);
+            SME_CUDA(cudaStreamEndCapture(G.stream, &graph));
+            cudaError_t e = cudaGraphInstantiate(&G.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            SME_CUDA(e);
+            std::memcpy(G.key, key, sizeof(key));
+        }
+        SME_CUDA(cudaGraphLaunch(G.exec, s));
     }
     if (timed) {
         SME_CUDA(cudaEventRecord(op->ev_loop[1], s));
@@ -498,6 +566,22 @@ static sme_status estimate_t(sme_op op, const real *u, const real *v, int t, int
     return SME_OK;
 }
 
+sme_status equilibrate_sparse(sme_op op, const sme_equil_params *p, void *u, void *v, void *ub, void *vb,
+                              cudaStream_t s)
+{
+    if (op->dbl) return equilibrate_t<double>(op, p, (double *)u, (double *)v, (double *)ub, (double *)vb, s);
+    return equilibrate_t<float>(op, p, (float *)u, (float *)v, (float *)ub, (float *)vb, s);
+}
+
+sme_status estimate_sparse(sme_op op, const void *u, const void *v, int t, int k, uint64_t seed, int sb, void *zu,
+                           void *zv, cudaStream_t s)
+{
+    if (op->batch) op->batch->sid_base = (uint32_t)sb;
+    if (op->dbl)
+        return estimate_t<double>(op, (const double *)u, (const double *)v, t, k, seed, sb, (double *)zu, (double *)zv, s);
+    return estimate_t<float>(op, (const float *)u, (const float *)v, t, k, seed, sb, (float *)zu, (float *)zv, s);
+}
+
 }  // namespace sme
 
 using namespace sme;
@@ -521,6 +605,10 @@ extern "C" sme_status sme_equilibrate(sme_op op, const sme_equil_params *p, void
 {
     if (!op || !p || !u || !v || !u_bar || !v_bar || p->T < 0 || p->t_begin < 1 || p->t0 < 0) {
         set_error("sme_equilibrate: bad arguments");
+        return SME_ERR_ARG;
+    }
+    if (op->batch) {
+        set_error("sme_equilibrate: the operator of a batch is driven by sme_batch_equilibrate");
         return SME_ERR_ARG;
     }
     if (!op->dense && !k_supported(p->k)) {
@@ -556,9 +644,5 @@ extern "C" sme_status sme_estimate(sme_op op, const void *u, const void *v, int3
         return dense_estimate(op, (const float *)u, (const float *)v, t, k, seed, stream_base, (float *)z_u,
                               (float *)z_v, (cudaStream_t)stream);
     }
-    if (op->dbl)
-        return estimate_t<double>(op, (const double *)u, (const double *)v, t, k, seed, stream_base, (double *)z_u,
-                                  (double *)z_v, (cudaStream_t)stream);
-    return estimate_t<float>(op, (const float *)u, (const float *)v, t, k, seed, stream_base, (float *)z_u,
-                             (float *)z_v, (cudaStream_t)stream);
+    return estimate_sparse(op, u, v, t, k, seed, stream_base, z_u, z_v, (cudaStream_t)stream);
 }

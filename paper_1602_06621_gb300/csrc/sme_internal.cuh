@@ -121,6 +121,16 @@ struct GraphCache {
 
 struct DenseOp;  // tensor-core operator (dense A)
 
+// A batch of matrices held as one block-diagonal operator (batch.cu).
+struct BatchInfo {
+    int32_t count = 0;
+    int32_t *mid[2] = {nullptr, nullptr};  // matrix id per sorted row [0] / sorted column [1]
+    int32_t *loc[2] = {nullptr, nullptr};  // index inside its matrix
+    void *tgt2[2] = {nullptr, nullptr};    // per matrix alpha^2 [0], beta^2 [1] (state type)
+    uint32_t sid_base = 0;                 // Philox stream of matrix b: sid_base + 2b (s), + 2b + 1 (w)
+    int64_t *row_off = nullptr, *col_off = nullptr;  // host, count + 1
+};
+
 }  // namespace sme
 
 struct sme_op_s {
@@ -131,6 +141,7 @@ struct sme_op_s {
     sme::Workspace ws;
     sme::GraphCache graph;
     sme::DenseOp *dense = nullptr;
+    sme::BatchInfo *batch = nullptr;
     int *d_status = nullptr;
     int64_t device_bytes = 0;
     cudaEvent_t ev_loop[2] = {nullptr, nullptr};  // SME_EQ_TIMED
@@ -154,6 +165,15 @@ sme_status build_sparse(sme_op op, const int32_t *d_row_ptr, const int32_t *d_co
 
 // Equilibration / estimation launches (equilibrate.cu).
 sme_status ensure_equil_workspace(sme_op op, int kw);
+sme_status equilibrate_sparse(sme_op op, const sme_equil_params *p, void *u, void *v, void *ub, void *vb,
+                              cudaStream_t s);
+sme_status estimate_sparse(sme_op op, const void *u, const void *v, int t, int k, uint64_t seed, int sb, void *zu,
+                           void *zv, cudaStream_t s);
+bool probes_supported(int k);
+
+// Host-side CSR validation (api.cu).
+sme_status validate_csr_host(int64_t m, int64_t n, int64_t nnz, const int32_t *rp, const int32_t *col,
+                             const void *vals, sme_dtype dtype);
 
 // LSQR and evaluation (lsqr.cu).
 void release_lsqr(sme_op op);

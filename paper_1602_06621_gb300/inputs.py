@@ -167,3 +167,15 @@ def workload_large(scale: float = 1.0, seed: int = 2) -> CSR:
     m = max(64, int(round(1_000_000 * scale)))
     n = max(32, int(round(500_000 * scale)))
     return sparse_fixed_row_nnz(m, n, 20, seed, var=2.0, dtype=np.float32)
+
+
+def batched_family(count: int, m_lo: int, m_hi: int, seed: int, *, nnz_lo: int = 5, nnz_hi: int = 50,
+                   var: float = 2.0, dtype=np.float32):
+    """count matrices: m log-uniform in [m_lo, m_hi], n = round(m * U[0.3, 1.0]), row lengths uniform
+    integers in [nnz_lo, nnz_hi] (capped at n), factors of variance `var`."""
+    rng = np.random.default_rng(seed)
+    ms = np.exp(rng.uniform(np.log(m_lo), np.log(m_hi), size=count)).round().astype(np.int64)
+    ns = np.maximum(1, np.round(ms * rng.uniform(0.3, 1.0, size=count))).astype(np.int64)
+    seeds = rng.integers(0, 2 ** 31, size=count)
+    return [sparse_variable_row_nnz(int(m), int(n), nnz_lo, nnz_hi, int(s), var=var, dtype=dtype)
+            for m, n, s in zip(ms, ns, seeds)]

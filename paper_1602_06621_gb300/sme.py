@@ -18,7 +18,8 @@ __all__ = [
     "SmeError", "load", "SME_F64", "SME_F32", "SME_BF16", "SME_FP8E4M3", "SME_EQ_ASYNC", "SME_EQ_NO_GRAPH", "SME_EQ_TIMED",
     "sme_op_create_csr", "sme_op_create_dense", "sme_op_destroy", "sme_op_get_info", "sme_draw_probes",
     "sme_equilibrate", "sme_op_check", "sme_estimate", "sme_evaluate", "sme_lsqr", "sme_status_string",
-    "default_params", "sme_estimate_rows_static", "SME_STATIC_MAX_COLS",
+    "default_params", "sme_estimate_rows_static", "SME_STATIC_MAX_COLS", "sme_batch_create", "sme_batch_destroy",
+    "sme_batch_get_info", "sme_batch_equilibrate", "sme_batch_estimate", "sme_batch_op",
 ]
 SME_STATIC_MAX_COLS = 1 << 20
 
@@ -83,6 +84,12 @@ SIGNATURES = {
     "sme_lsqr": ([_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(sme_lsqr_params), ctypes.POINTER(sme_lsqr_result), _vp],
                  _i32),
     "sme_estimate_rows_static": ([_i64, _i64, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _u64, _i32, _vp, _vp], _i32),
+    "sme_batch_create": ([ctypes.POINTER(_vp), _i32, _vp, _vp, _vp, _vp, _vp, _i32, _vp], _i32),
+    "sme_batch_destroy": ([_vp], _i32),
+    "sme_batch_get_info": ([_vp, ctypes.POINTER(_i32), _vp, _vp], _i32),
+    "sme_batch_equilibrate": ([_vp, ctypes.POINTER(sme_equil_params), _vp, _vp, _vp, _vp, _vp], _i32),
+    "sme_batch_estimate": ([_vp, _vp, _vp, _i32, _i32, _u64, _i32, _vp, _vp, _vp], _i32),
+    "sme_batch_op": ([_vp, ctypes.POINTER(_vp)], _i32),
 }
 
 
@@ -221,3 +228,62 @@ def sme_estimate_rows_static(m, n, row_ptr, col_idx, vals, u, v, t, k, seed, str
     _check(load().sme_estimate_rows_static(int(m), int(n), _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(u), _ptr(v),
                                            int(t), int(k), int(seed), int(stream_base), _ptr(z_u), _stream(stream)),
            "sme_estimate_rows_static")
+
+
+def sme_batch_create(mats, dtype=None, stream=None):
+    """Create a batch from a list of CSR matrices (objects with m, n, row_ptr, col_idx, vals; host NumPy)."""
+    if dtype is None:
+        dtype = SME_F64 if mats[0].vals.dtype == np.float64 else SME_F32
+    vt = np.float64 if dtype == SME_F64 else np.float32
+    keep = []
+    B = len(mats)
+    ms = np.array([A.m for A in mats], np.int64)
+    ns = np.array([A.n for A in mats], np.int64)
+    rps = (ctypes.c_void_p * B)()
+    cis = (ctypes.c_void_p * B)()
+    vas = (ctypes.c_void_p * B)()
+    for i, A in enumerate(mats):
+        rp = np.ascontiguousarray(A.row_ptr, dtype=np.int32)
+        ci = np.ascontiguousarray(A.col_idx, dtype=np.int32)
+        va = np.ascontiguousarray(A.vals, dtype=vt)
+        keep += [rp, ci, va]
+        rps[i], cis[i], vas[i] = rp.ctypes.data, ci.ctypes.data, va.ctypes.data
+    b = ctypes.c_void_p()
+    st = load().sme_batch_create(ctypes.byref(b), B, _ptr(ms), _ptr(ns), ctypes.cast(rps, ctypes.c_void_p),
+                                 ctypes.cast(cis, ctypes.c_void_p), ctypes.cast(vas, ctypes.c_void_p), int(dtype),
+                                 _stream(stream))
+    _check(st, "sme_batch_create")
+    return b
+
+
+def sme_batch_destroy(b):
+    if b:
+        _check(load().sme_batch_destroy(b), "sme_batch_destroy")
+
+
+def sme_batch_get_info(b):
+    count = ctypes.c_int32()
+    _check(load().sme_batch_get_info(b, ctypes.byref(count), None, None), "sme_batch_get_info")
+    ro = np.zeros(count.value + 1, np.int64)
+    co = np.zeros(count.value + 1, np.int64)
+    _check(load().sme_batch_get_info(b, None, _ptr(ro), _ptr(co)), "sme_batch_get_info")
+    return count.value, ro, co
+
+
+def sme_batch_equilibrate(b, u, v, u_bar, v_bar, *, T, k, t_begin=1, t0=0, seed=0, stream_base=0, alpha=0.0,
+                          beta=0.0, gamma=0.0, M=0.0, flags=0, stream=None):
+    p = sme_equil_params(alpha, beta, gamma, M, int(T), int(k), int(t_begin), int(t0), int(seed), int(stream_base),
+                         int(flags))
+    _check(load().sme_batch_equilibrate(b, ctypes.byref(p), _ptr(u), _ptr(v), _ptr(u_bar), _ptr(v_bar),
+                                        _stream(stream)), "sme_batch_equilibrate")
+
+
+def sme_batch_estimate(b, u, v, t, k, seed, stream_base, z_u, z_v, stream=None):
+    _check(load().sme_batch_estimate(b, _ptr(u), _ptr(v), int(t), int(k), int(seed), int(stream_base), _ptr(z_u),
+                                     _ptr(z_v), _stream(stream)), "sme_batch_estimate")
+
+
+def sme_batch_op(b):
+    op = ctypes.c_void_p()
+    _check(load().sme_batch_op(b, ctypes.byref(op)), "sme_batch_op")
+    return op

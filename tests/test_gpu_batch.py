@@ -1,0 +1,109 @@
+"""Batches of matrices (one block-diagonal operator) against separate runs and the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1602_06621_gb300 import inputs as I
+from paper_1602_06621_gb300 import sme
+
+from gpu_util import gpu_equilibrate, make_op, rel_norm
+
+pytestmark = pytest.mark.gpu
+
+
+def _zeros(n, td):
+    import torch
+    return torch.zeros(n, dtype=td, device="cuda")
+
+
+def _batch_run(b, mats, td, **kw):
+    M = sum(A.m for A in mats)
+    N = sum(A.n for A in mats)
+    u, v, ub, vb = _zeros(M, td), _zeros(N, td), _zeros(M, td), _zeros(N, td)
+    sme.sme_batch_equilibrate(b, u, v, ub, vb, **kw)
+    return [x.cpu().double().numpy() for x in (u, v, ub, vb)]
+
+
+@pytest.mark.parametrize("k", [16, 32])
+def test_batch_equals_separate_runs_bitwise(k):
+    import torch
+    mats = I.batched_family(7, 60, 3000, seed=k)
+    b = sme.sme_batch_create(mats)
+    try:
+        count, ro, co = sme.sme_batch_get_info(b)
+        assert count == 7 and ro[-1] == sum(A.m for A in mats)
+        got = _batch_run(b, mats, torch.float32, T=25, k=k, seed=4, stream_base=6)
+    finally:
+        sme.sme_batch_destroy(b)
+    for i, A in enumerate(mats):
+        op, dt = make_op(A)
+        try:
+            one = gpu_equilibrate(op, dt, A.m, A.n, T=25, k=k, seed=4, stream_base=6 + 2 * i)
+        finally:
+            sme.sme_op_destroy(op)
+        sl = [slice(ro[i], ro[i + 1]), slice(co[i], co[i + 1]), slice(ro[i], ro[i + 1]), slice(co[i], co[i + 1])]
+        for x, s_, y in zip(got, sl, one):
+            np.testing.assert_array_equal(x[s_], y)
+
+
+def test_batch_fp64_matches_oracle_per_matrix():
+    import torch
+    mats = I.batched_family(5, 40, 400, seed=3, dtype=np.float64)
+    b = sme.sme_batch_create(mats)
+    try:
+        _, ro, co = sme.sme_batch_get_info(b)
+        got = _batch_run(b, mats, torch.float64, T=6, k=8, seed=2)
+    finally:
+        sme.sme_batch_destroy(b)
+    for i, A in enumerate(mats):
+        ref = O.equilibrate(A, T=6, k=8, seed=2, stream_base=2 * i)
+        mine = (got[0][ro[i]:ro[i + 1]], got[1][co[i]:co[i + 1]], got[2][ro[i]:ro[i + 1]], got[3][co[i]:co[i + 1]])
+        assert rel_norm(mine, ref) <= 1e-10
+
+
+def test_batch_estimate_and_evaluate():
+    import torch
+    mats = I.batched_family(4, 100, 900, seed=8)
+    b = sme.sme_batch_create(mats)
+    try:
+        _, ro, co = sme.sme_batch_get_info(b)
+        rng = np.random.default_rng(0)
+        u = rng.normal(0, 0.5, ro[-1]).astype(np.float32)
+        v = rng.normal(0, 0.5, co[-1]).astype(np.float32)
+        ud, vd = torch.tensor(u, device="cuda"), torch.tensor(v, device="cuda")
+        zu, zv = _zeros(ro[-1], torch.float32), _zeros(co[-1], torch.float32)
+        sme.sme_batch_estimate(b, ud, vd, 3, 16, 5, 0, zu, zv)
+        r2 = _zeros(ro[-1], torch.float64)
+        c2 = _zeros(co[-1], torch.float64)
+        sme.sme_evaluate(sme.sme_batch_op(b), ud, vd, r2=r2, c2=c2)
+        zu, zv, r2, c2 = (x.cpu().double().numpy() for x in (zu, zv, r2, c2))
+    finally:
+        sme.sme_batch_destroy(b)
+    for i, A in enumerate(mats):
+        A64 = O.OracleCSR.from_any(A)
+        ui, vi = u[ro[i]:ro[i + 1]], v[co[i]:co[i + 1]]
+        er2, ec2 = O.exact_norms_sq(A64, ui, vi)
+        np.testing.assert_allclose(r2[ro[i]:ro[i + 1]], er2, rtol=1e-12)
+        np.testing.assert_allclose(c2[co[i]:co[i + 1]], ec2, rtol=1e-12)
+        ez = O.row_estimate(A64, ui, vi, O.probe_signs(5, 3, 2 * i, A.n, 16))
+        ezv = O.col_estimate(A64, ui, vi, O.probe_signs(5, 3, 2 * i + 1, A.m, 16))
+        assert np.all(np.abs(zu[ro[i]:ro[i + 1]] - ez) <= 3e-5 * er2 + 1e-30)
+        assert np.all(np.abs(zv[co[i]:co[i + 1]] - ezv) <= 3e-5 * ec2 + 1e-30)
+
+
+def test_graph_replay_equals_direct_launches():
+    A = I.workload_large(scale=0.004, seed=4)
+    op, dt = make_op(A)
+    try:
+        g1 = gpu_equilibrate(op, dt, A.m, A.n, T=30, k=32, seed=1)
+        g2 = gpu_equilibrate(op, dt, A.m, A.n, T=30, k=32, seed=1)  # replays the cached graph
+        d1 = gpu_equilibrate(op, dt, A.m, A.n, T=30, k=32, seed=1, flags=sme.SME_EQ_NO_GRAPH)
+        g3 = gpu_equilibrate(op, dt, A.m, A.n, T=30, k=32, seed=2)  # new key: captured again
+        d3 = gpu_equilibrate(op, dt, A.m, A.n, T=30, k=32, seed=2, flags=sme.SME_EQ_NO_GRAPH)
+    finally:
+        sme.sme_op_destroy(op)
+    for a, b_, c in zip(g1, g2, d1):
+        np.testing.assert_array_equal(a, b_)
+        np.testing.assert_array_equal(a, c)
+    for a, c in zip(g3, d3):
+        np.testing.assert_array_equal(a, c)
