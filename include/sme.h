@@ -154,6 +154,17 @@ typedef struct {
 sme_status sme_equilibrate(sme_op op, const sme_equil_params *p, void *u, void *v, void *u_bar, void *v_bar,
                            void *stream);
 
+/*
+ * sme_op_autotune -- choose the launch shape of the iteration kernel for probe count k on this sparse
+ * operator: 32-row slices per CTA (4, 8 or 16; FP32 with k = 16 or 32, otherwise 8) and whether the
+ * A^T CTAs are dispatched before the A CTAs.  Every candidate is timed (CUDA events, estimate mode) and
+ * the fastest is kept for later calls with this k.  Outputs are optional host pointers.  The rows'
+ * ordering (the length sort of the sliced ELL) is fixed at creation.  sme_batch_equilibrate calls this
+ * on its first use of a k.  Synchronises `stream`.
+ */
+sme_status sme_op_autotune(sme_op op, int32_t k, int32_t *slices_per_cta, int32_t *cols_first,
+                           float *ms_per_iteration, void *stream);
+
 /* sme_op_check -- synchronise `stream`, return and clear the op's device status word. */
 sme_status sme_op_check(sme_op op, void *stream);
 

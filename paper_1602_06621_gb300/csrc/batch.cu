@@ -188,6 +188,10 @@ extern "C" sme_status sme_batch_equilibrate(sme_batch b, const sme_equil_params 
             SME_CUDA(cudaStreamSynchronize(s));
         }
     }
+    // First call with this k: choose the launch shape for this batch (sme_op_autotune).
+    int slot = 0;
+    while ((1 << slot) < p->k) ++slot;
+    if (op->tuned[slot].spc == 0) SME_TRY(autotune_sparse(op, p->k, s, nullptr, nullptr, nullptr));
     SME_TRY(equilibrate_sparse(op, p, u, v, u_bar, v_bar, s));
     if (p->flags & SME_EQ_ASYNC) return SME_OK;
     return sme_op_check(op, stream);

@@ -22,8 +22,7 @@
 
 namespace sme {
 
-constexpr int ITER_THREADS = 256;
-constexpr int SLICES_PER_CTA = ITER_THREADS / 32;
+constexpr int DEFAULT_SPC = 8;  // 32-row slices per CTA unless the autotuner chose otherwise
 
 struct SellArgs {
     const int64_t *slice_off;
@@ -46,7 +45,8 @@ struct StepArgs {
     real gamma, M, eta, avg_new, avg_old;
     uint32_t t_next, key0, key1;
     uint32_t sid_out[2];    // Philox stream of the table each side writes: rows -> w, columns -> s
-    int64_t blocks0;
+    int64_t blocks0;        // CTAs of the first group
+    int cols_first;         // 1: the first group is the column side
     int mode;               // 0: full step, 1: estimate only
     int *status;
     // Batches of matrices (block-diagonal operator): per sorted row / column the matrix id and the
@@ -200,17 +200,18 @@ __device__ __forceinline__ double dclip(double x, double M) { return fmin(fmax(x
 
 // ------------------------------------------------------------------ the iteration kernel
 
-template <typename real, int K>
-__global__ void __launch_bounds__(ITER_THREADS) sgd_iteration(StepArgs<real> a)
+template <typename real, int K, int SPC>
+__global__ void __launch_bounds__(SPC * 32) sgd_iteration(StepArgs<real> a)
 {
     constexpr int KW = (K + 31) / 32;
     using Tab = TabEntry<real, KW>;
     // Select this CTA's side with per-field selects (no dynamic indexing into the parameter block).
-    const bool cols = (int64_t)blockIdx.x >= a.blocks0;
-    const int64_t blk = cols ? (int64_t)blockIdx.x - a.blocks0 : (int64_t)blockIdx.x;
+    const bool first = (int64_t)blockIdx.x < a.blocks0;
+    const bool cols = a.cols_first ? first : !first;
+    const int64_t blk = first ? (int64_t)blockIdx.x : (int64_t)blockIdx.x - a.blocks0;
     const SellArgs S = cols ? a.A[1] : a.A[0];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t slice = blk * SLICES_PER_CTA + warp;
+    const int64_t slice = blk * SPC + warp;
     if (slice >= S.nslices) return;
     const int64_t r = slice * 32 + lane;
 
@@ -384,19 +385,64 @@ static SellArgs sell_args(const Sell &S)
     return SellArgs{S.slice_off, S.slice_w, S.ent, S.val64, S.perm, S.rows, S.nslices};
 }
 
+template <typename real, int K>
+static void launch_k(const StepArgs<real> &a, int spc, unsigned grid, cudaStream_t s)
+{
+    if (sizeof(real) == 4 && (K == 16 || K == 32)) {
+        if (spc == 4) {
+            sgd_iteration<real, K, 4><<<grid, 4 * 32, 0, s>>>(a);
+            return;
+        }
+        if (spc == 16) {
+            sgd_iteration<real, K, 16><<<grid, 16 * 32, 0, s>>>(a);
+            return;
+        }
+    }
+    sgd_iteration<real, K, DEFAULT_SPC><<<grid, DEFAULT_SPC * 32, 0, s>>>(a);
+}
+
 template <typename real>
-static void launch_iteration(const StepArgs<real> &a, int k, unsigned grid, cudaStream_t s)
+static void launch_iteration(const StepArgs<real> &a, int k, int spc, unsigned grid, cudaStream_t s)
 {
     switch (k) {
-        case 1: sgd_iteration<real, 1><<<grid, ITER_THREADS, 0, s>>>(a); break;
-        case 2: sgd_iteration<real, 2><<<grid, ITER_THREADS, 0, s>>>(a); break;
-        case 4: sgd_iteration<real, 4><<<grid, ITER_THREADS, 0, s>>>(a); break;
-        case 8: sgd_iteration<real, 8><<<grid, ITER_THREADS, 0, s>>>(a); break;
-        case 16: sgd_iteration<real, 16><<<grid, ITER_THREADS, 0, s>>>(a); break;
-        case 32: sgd_iteration<real, 32><<<grid, ITER_THREADS, 0, s>>>(a); break;
-        case 64: sgd_iteration<real, 64><<<grid, ITER_THREADS, 0, s>>>(a); break;
+        case 1: launch_k<real, 1>(a, spc, grid, s); break;
+        case 2: launch_k<real, 2>(a, spc, grid, s); break;
+        case 4: launch_k<real, 4>(a, spc, grid, s); break;
+        case 8: launch_k<real, 8>(a, spc, grid, s); break;
+        case 16: launch_k<real, 16>(a, spc, grid, s); break;
+        case 32: launch_k<real, 32>(a, spc, grid, s); break;
+        case 64: launch_k<real, 64>(a, spc, grid, s); break;
         default: break;
     }
+}
+
+// Launch shape chosen for probe count k: slices per CTA and which side's CTAs come first.
+struct Shape {
+    int spc = DEFAULT_SPC;
+    int cols_first = 0;
+};
+
+static int k_slot(int k)
+{
+    int b = 0;
+    while ((1 << b) < k) ++b;
+    return b;
+}
+
+static Shape shape_for(sme_op op, int k)
+{
+    Shape sh;
+    const int slot = k_slot(k);
+    if (slot < 8 && op->tuned[slot].spc > 0) {
+        sh.spc = op->tuned[slot].spc;
+        sh.cols_first = op->tuned[slot].cols_first;
+    }
+    return sh;
+}
+
+static unsigned grid_for(sme_op op, const Shape &sh)
+{
+    return (unsigned)((op->fwd.nslices + sh.spc - 1) / sh.spc + (op->bwd.nslices + sh.spc - 1) / sh.spc);
 }
 
 template <typename real>
@@ -432,7 +478,7 @@ static Resolved resolve(sme_op op, double alpha, double beta, double gamma, doub
 }
 
 template <typename real>
-static StepArgs<real> base_args(sme_op op, int buf_in, const Resolved &R, uint64_t seed)
+static StepArgs<real> base_args(sme_op op, int buf_in, const Resolved &R, uint64_t seed, const Shape &sh)
 {
     StepArgs<real> a{};
     a.A[0] = sell_args(op->fwd);
@@ -451,7 +497,9 @@ static StepArgs<real> base_args(sme_op op, int buf_in, const Resolved &R, uint64
     a.M = (real)R.M;
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
-    a.blocks0 = (op->fwd.nslices + SLICES_PER_CTA - 1) / SLICES_PER_CTA;
+    const int64_t br = (op->fwd.nslices + sh.spc - 1) / sh.spc, bc = (op->bwd.nslices + sh.spc - 1) / sh.spc;
+    a.cols_first = sh.cols_first;
+    a.blocks0 = sh.cols_first ? bc : br;
     a.status = op->d_status;
     if (op->batch) {
         for (int side = 0; side < 2; ++side) {
@@ -464,11 +512,6 @@ static StepArgs<real> base_args(sme_op op, int buf_in, const Resolved &R, uint64
     return a;
 }
 
-static unsigned iter_grid(sme_op op)
-{
-    return (unsigned)((op->fwd.nslices + SLICES_PER_CTA - 1) / SLICES_PER_CTA +
-                      (op->bwd.nslices + SLICES_PER_CTA - 1) / SLICES_PER_CTA);
-}
 
 template <typename real>
 static sme_status equilibrate_t(sme_op op, const sme_equil_params *p, real *u, real *v, real *ub, real *vb,
@@ -485,7 +528,8 @@ static sme_status equilibrate_t(sme_op op, const sme_equil_params *p, real *u, r
                       p->seed, s);
     launch_load<real>(op, 1, kw, v, vb, (real *)op->ws.v, (real *)op->ws.vb, op->ws.tab_v[buf], (uint32_t)tb, sid_s,
                       p->seed, s);
-    const unsigned grid = iter_grid(op);
+    const Shape sh = shape_for(op, k);
+    const unsigned grid = grid_for(op, sh);
     const bool timed = (p->flags & SME_EQ_TIMED) != 0;
     if (timed) {
         for (int i = 0; i < 2; ++i)
@@ -494,7 +538,7 @@ static sme_status equilibrate_t(sme_op op, const sme_equil_params *p, real *u, r
     }
     auto enqueue = [&](cudaStream_t q) {
         for (int t = tb; t < tb + p->T; ++t) {
-            StepArgs<real> a = base_args<real>(op, t & 1, R, p->seed);
+            StepArgs<real> a = base_args<real>(op, t & 1, R, p->seed, sh);
             a.eta = (real)(2.0 / (R.gamma * ((double)t + (double)p->t0 + 1.0)));
             a.avg_new = (real)(2.0 / ((double)t + 2.0));
             a.avg_old = (real)((double)t / ((double)t + 2.0));
@@ -502,7 +546,7 @@ static sme_status equilibrate_t(sme_op op, const sme_equil_params *p, real *u, r
             a.sid_out[0] = sid_w;
             a.sid_out[1] = sid_s;
             a.mode = 0;
-            launch_iteration<real>(a, k, grid, q);
+            launch_iteration<real>(a, k, sh.spc, grid, q);
         }
     };
     if ((p->flags & SME_EQ_NO_GRAPH) || p->T < 2) {
@@ -512,7 +556,7 @@ static sme_status equilibrate_t(sme_op op, const sme_equil_params *p, real *u, r
         // so one captured graph is replayed for repeated calls with the same parameters.
         const int64_t key[12] = {p->T, p->k, p->t_begin, p->t0, (int64_t)p->seed, p->stream_base,
                                  (int64_t)(R.alpha * 1e15), (int64_t)(R.beta * 1e15), (int64_t)(R.gamma * 1e15),
-                                 (int64_t)(R.M * 1e15), (int64_t)op->ws.tab_bytes_u, 1};
+                                 (int64_t)(R.M * 1e15), (int64_t)op->ws.tab_bytes_u, sh.spc * 2 + sh.cols_first};
         GraphCache &G = op->graph;
         if (!G.exec || std::memcmp(G.key, key, sizeof(key)) != 0) {
             if (G.exec) {
@@ -554,16 +598,76 @@ static sme_status estimate_t(sme_op op, const real *u, const real *v, int t, int
                       (uint32_t)sb + 1u, seed, s);
     launch_load<real>(op, 1, kw, v, nullptr, (real *)op->ws.v, nullptr, op->ws.tab_v[buf], (uint32_t)t, (uint32_t)sb,
                       seed, s);
-    StepArgs<real> a = base_args<real>(op, buf, R, seed);
+    const Shape sh = shape_for(op, k);
+    StepArgs<real> a = base_args<real>(op, buf, R, seed, sh);
     a.mode = 1;
     a.z[0] = zu;
     a.z[1] = zv;
     // A NULL output skips that side by giving it no slices.
     if (!zu) a.A[0].nslices = 0;
     if (!zv) a.A[1].nslices = 0;
-    launch_iteration<real>(a, k, iter_grid(op), s);
+    launch_iteration<real>(a, k, sh.spc, grid_for(op, sh), s);
     SME_CUDA(cudaGetLastError());
     return SME_OK;
+}
+
+// Times every launch shape on this operator (estimate mode, zero state) and keeps the fastest for k.
+template <typename real>
+static sme_status autotune_t(sme_op op, int k, cudaStream_t s, int *spc_out, int *cf_out, float *ms_out)
+{
+    const int kw = (k + 31) / 32;
+    SME_TRY(ensure_equil_workspace(op, kw));
+    const Resolved R = resolve(op, 0, 0, 0, 0);
+    launch_load<real>(op, 0, kw, (const real *)nullptr, nullptr, (real *)op->ws.u, nullptr, op->ws.tab_u[0], 1u, 1u,
+                      0, s);
+    launch_load<real>(op, 1, kw, (const real *)nullptr, nullptr, (real *)op->ws.v, nullptr, op->ws.tab_v[0], 1u, 0u,
+                      0, s);
+    cudaEvent_t e0, e1;
+    SME_CUDA(cudaEventCreate(&e0));
+    SME_CUDA(cudaEventCreate(&e1));
+    const int spcs[3] = {4, 8, 16};
+    float best = 1e30f;
+    Shape best_sh;
+    for (int cf = 0; cf < 2; ++cf)
+        for (int i = 0; i < 3; ++i) {
+            Shape sh;
+            sh.spc = (sizeof(real) == 4 && (k == 16 || k == 32)) ? spcs[i] : DEFAULT_SPC;
+            sh.cols_first = cf;
+            if (sh.spc != spcs[i] && i != 1) continue;
+            StepArgs<real> a = base_args<real>(op, 0, R, 0, sh);
+            a.mode = 1;
+            a.z[0] = (real *)op->ws.ub;
+            a.z[1] = (real *)op->ws.vb;
+            const unsigned grid = grid_for(op, sh);
+            for (int w = 0; w < 2; ++w) launch_iteration<real>(a, k, sh.spc, grid, s);
+            SME_CUDA(cudaEventRecord(e0, s));
+            for (int r = 0; r < 5; ++r) launch_iteration<real>(a, k, sh.spc, grid, s);
+            SME_CUDA(cudaEventRecord(e1, s));
+            SME_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            SME_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_sh = sh;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const int slot = k_slot(k);
+    if (slot < 8) {
+        op->tuned[slot].spc = best_sh.spc;
+        op->tuned[slot].cols_first = best_sh.cols_first;
+    }
+    if (spc_out) *spc_out = best_sh.spc;
+    if (cf_out) *cf_out = best_sh.cols_first;
+    if (ms_out) *ms_out = best / 5.f;
+    return SME_OK;
+}
+
+sme_status autotune_sparse(sme_op op, int k, cudaStream_t s, int *spc, int *cols_first, float *ms)
+{
+    if (op->dbl) return autotune_t<double>(op, k, s, spc, cols_first, ms);
+    return autotune_t<float>(op, k, s, spc, cols_first, ms);
 }
 
 sme_status equilibrate_sparse(sme_op op, const sme_equil_params *p, void *u, void *v, void *ub, void *vb,
@@ -627,6 +731,27 @@ extern "C" sme_status sme_equilibrate(sme_op op, const sme_equil_params *p, void
     }
     if (p->flags & SME_EQ_ASYNC) return SME_OK;
     return sme_op_check(op, stream);
+}
+
+extern "C" sme_status sme_op_autotune(sme_op op, int32_t k, int32_t *slices_per_cta, int32_t *cols_first,
+                                      float *ms_per_iteration, void *stream)
+{
+    if (!op || op->dense) {
+        set_error("sme_op_autotune: sparse operators only");
+        return SME_ERR_ARG;
+    }
+    if (!k_supported(k)) {
+        set_error("sme_op_autotune: k=%d not supported", k);
+        return SME_ERR_UNSUPPORTED;
+    }
+    int spc = 0, cf = 0;
+    float ms = 0.f;
+    if (op->batch) op->batch->sid_base = 0;
+    SME_TRY(autotune_sparse(op, k, (cudaStream_t)stream, &spc, &cf, &ms));
+    if (slices_per_cta) *slices_per_cta = spc;
+    if (cols_first) *cols_first = cf;
+    if (ms_per_iteration) *ms_per_iteration = ms;
+    return SME_OK;
 }
 
 extern "C" sme_status sme_estimate(sme_op op, const void *u, const void *v, int32_t t, int32_t k, uint64_t seed,

@@ -144,6 +144,9 @@ struct sme_op_s {
     sme::BatchInfo *batch = nullptr;
     int *d_status = nullptr;
     int64_t device_bytes = 0;
+    struct {
+        int spc = 0, cols_first = 0;
+    } tuned[8];                                    // launch shape per log2(k), 0 = default
     cudaEvent_t ev_loop[2] = {nullptr, nullptr};  // SME_EQ_TIMED
     bool loop_timed = false;
     int64_t loop_iters = 0;
@@ -170,6 +173,7 @@ sme_status equilibrate_sparse(sme_op op, const sme_equil_params *p, void *u, voi
 sme_status estimate_sparse(sme_op op, const void *u, const void *v, int t, int k, uint64_t seed, int sb, void *zu,
                            void *zv, cudaStream_t s);
 bool probes_supported(int k);
+sme_status autotune_sparse(sme_op op, int k, cudaStream_t s, int *spc, int *cols_first, float *ms);
 
 // Host-side CSR validation (api.cu).
 sme_status validate_csr_host(int64_t m, int64_t n, int64_t nnz, const int32_t *rp, const int32_t *col,

@@ -19,7 +19,7 @@ __all__ = [
     "sme_op_create_csr", "sme_op_create_dense", "sme_op_destroy", "sme_op_get_info", "sme_draw_probes",
     "sme_equilibrate", "sme_op_check", "sme_estimate", "sme_evaluate", "sme_lsqr", "sme_status_string",
     "default_params", "sme_estimate_rows_static", "SME_STATIC_MAX_COLS", "sme_batch_create", "sme_batch_destroy",
-    "sme_batch_get_info", "sme_batch_equilibrate", "sme_batch_estimate", "sme_batch_op",
+    "sme_batch_get_info", "sme_batch_equilibrate", "sme_batch_estimate", "sme_batch_op", "sme_op_autotune",
 ]
 SME_STATIC_MAX_COLS = 1 << 20
 
@@ -90,6 +90,8 @@ SIGNATURES = {
     "sme_batch_equilibrate": ([_vp, ctypes.POINTER(sme_equil_params), _vp, _vp, _vp, _vp, _vp], _i32),
     "sme_batch_estimate": ([_vp, _vp, _vp, _i32, _i32, _u64, _i32, _vp, _vp, _vp], _i32),
     "sme_batch_op": ([_vp, ctypes.POINTER(_vp)], _i32),
+    "sme_op_autotune": ([_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float), _vp],
+                        _i32),
 }
 
 
@@ -287,3 +289,10 @@ def sme_batch_op(b):
     op = ctypes.c_void_p()
     _check(load().sme_batch_op(b, ctypes.byref(op)), "sme_batch_op")
     return op
+
+
+def sme_op_autotune(op, k, stream=None) -> dict:
+    spc, cf, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(load().sme_op_autotune(op, int(k), ctypes.byref(spc), ctypes.byref(cf), ctypes.byref(ms), _stream(stream)),
+           "sme_op_autotune")
+    return {"slices_per_cta": spc.value, "cols_first": cf.value, "ms_per_iteration": ms.value}

@@ -107,3 +107,19 @@ def test_graph_replay_equals_direct_launches():
         np.testing.assert_array_equal(a, c)
     for a, c in zip(g3, d3):
         np.testing.assert_array_equal(a, c)
+
+
+def test_autotuned_shape_gives_identical_results():
+    """The launch shape changes only scheduling: results are bitwise those of the default shape."""
+    A = I.workload_large(scale=0.004, seed=5)
+    op, dt = make_op(A)
+    try:
+        ref = gpu_equilibrate(op, dt, A.m, A.n, T=12, k=32, seed=1)
+        choice = sme.sme_op_autotune(op, 32)
+        assert choice["slices_per_cta"] in (4, 8, 16) and choice["cols_first"] in (0, 1)
+        assert choice["ms_per_iteration"] > 0
+        got = gpu_equilibrate(op, dt, A.m, A.n, T=12, k=32, seed=1)
+    finally:
+        sme.sme_op_destroy(op)
+    for a, b_ in zip(ref, got):
+        np.testing.assert_array_equal(a, b_)
