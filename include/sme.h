@@ -265,6 +265,16 @@ sme_status sme_batch_equilibrate(sme_batch b, const sme_equil_params *p, void *u
 sme_status sme_batch_estimate(sme_batch b, const void *u, const void *v, int32_t t, int32_t k, uint64_t seed,
                               int32_t stream_base, void *z_u, void *z_v, void *stream);
 
+/*
+ * sme_batch_lsqr -- sme_lsqr for every matrix of the batch, each with its own LSQR (own FP64 scalar
+ * recurrence, own residual checks and convergence; a converged matrix stops changing while the others
+ * continue).  u_bar, v_bar (nullable), b and x are the concatenated vectors; results is a HOST array of
+ * one sme_lsqr_result per matrix (kernel_launches is reported in results[0]).  Returns
+ * SME_ERR_NOT_CONVERGED when any matrix stopped above tol (all results still written).  Synchronises.
+ */
+sme_status sme_batch_lsqr(sme_batch b, const void *u_bar, const void *v_bar, const void *bvec, void *x,
+                          const sme_lsqr_params *p, sme_lsqr_result *results, void *stream);
+
 /* The block-diagonal operator of the batch (owned by the batch; do not destroy it), for sme_evaluate
  * of all matrices at once (row / column norms come back concatenated). */
 sme_status sme_batch_op(sme_batch b, sme_op *op);

@@ -16,10 +16,6 @@
 
 #include "sme_internal.cuh"
 
-struct sme_batch_s {
-    sme_op op = nullptr;
-};
-
 namespace sme {
 
 __global__ void gather_meta(int64_t rows, const int32_t *perm, const int32_t *mid_orig, const int32_t *loc_orig,

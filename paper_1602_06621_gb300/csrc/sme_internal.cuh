@@ -152,6 +152,10 @@ struct sme_op_s {
     int64_t loop_iters = 0;
 };
 
+struct sme_batch_s {
+    sme_op op = nullptr;  // the block-diagonal operator (owned)
+};
+
 namespace sme {
 
 // Device allocation bookkeeping for an op.

@@ -19,7 +19,7 @@ __all__ = [
     "sme_op_create_csr", "sme_op_create_dense", "sme_op_destroy", "sme_op_get_info", "sme_draw_probes",
     "sme_equilibrate", "sme_op_check", "sme_estimate", "sme_evaluate", "sme_lsqr", "sme_status_string",
     "default_params", "sme_estimate_rows_static", "SME_STATIC_MAX_COLS", "sme_batch_create", "sme_batch_destroy",
-    "sme_batch_get_info", "sme_batch_equilibrate", "sme_batch_estimate", "sme_batch_op", "sme_op_autotune",
+    "sme_batch_get_info", "sme_batch_equilibrate", "sme_batch_estimate", "sme_batch_op", "sme_op_autotune", "sme_batch_lsqr",
 ]
 SME_STATIC_MAX_COLS = 1 << 20
 
@@ -92,6 +92,7 @@ SIGNATURES = {
     "sme_batch_op": ([_vp, ctypes.POINTER(_vp)], _i32),
     "sme_op_autotune": ([_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float), _vp],
                         _i32),
+    "sme_batch_lsqr": ([_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(sme_lsqr_params), _vp, _vp], _i32),
 }
 
 
@@ -296,3 +297,16 @@ def sme_op_autotune(op, k, stream=None) -> dict:
     _check(load().sme_op_autotune(op, int(k), ctypes.byref(spc), ctypes.byref(cf), ctypes.byref(ms), _stream(stream)),
            "sme_op_autotune")
     return {"slices_per_cta": spc.value, "cols_first": cf.value, "ms_per_iteration": ms.value}
+
+
+def sme_batch_lsqr(b, u_bar, v_bar, bvec, x, *, tol=1e-6, max_iters=100000, check_every=10, stop_rule=0, stream=None,
+                   raise_on_not_converged=False):
+    """Per-matrix LSQR over a batch; returns a list of per-matrix result dicts."""
+    count = sme_batch_get_info(b)[0]
+    p = sme_lsqr_params(float(tol), int(max_iters), int(check_every), int(stop_rule))
+    res = (sme_lsqr_result * count)()
+    st = load().sme_batch_lsqr(b, _ptr(u_bar), _ptr(v_bar), _ptr(bvec), _ptr(x), ctypes.byref(p),
+                               ctypes.cast(res, ctypes.c_void_p), _stream(stream))
+    if st != -7 or raise_on_not_converged:
+        _check(st, "sme_batch_lsqr")
+    return [{f: getattr(r, f) for f, _ in sme_lsqr_result._fields_} for r in res]

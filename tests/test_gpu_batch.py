@@ -123,3 +123,46 @@ def test_autotuned_shape_gives_identical_results():
         sme.sme_op_destroy(op)
     for a, b_ in zip(ref, got):
         np.testing.assert_array_equal(a, b_)
+
+
+def test_batch_lsqr_matches_per_matrix_lsqr():
+    """Each matrix of the batch gets its own LSQR.  Against sme_lsqr on the matrix alone (same scalings,
+    same right-hand side): the first iterates agree to rounding; converged solves agree in iteration count
+    within 2 % (the norms are summed in a different order, and LSQR amplifies rounding over hundreds of
+    iterations); every residual is re-checked by the oracle."""
+    import torch
+    mats = I.batched_family(5, 80, 1500, seed=21, dtype=np.float64)
+    b = sme.sme_batch_create(mats)
+    try:
+        _, ro, co = sme.sme_batch_get_info(b)
+        st = _batch_run(b, mats, torch.float64, T=60, k=16, seed=1)
+        ub, vb = (torch.tensor(x, device="cuda") for x in (st[2], st[3]))
+        bvecs = [O.csr_matvec(A, I.normal_vector(A.n, 30 + i)) for i, A in enumerate(mats)]
+        bcat = torch.tensor(np.concatenate(bvecs), device="cuda")
+        x5 = torch.zeros(int(co[-1]), dtype=torch.float64, device="cuda")
+        sme.sme_batch_lsqr(b, ub, vb, bcat, x5, tol=0.0, max_iters=5, check_every=5)
+        x5 = x5.cpu().numpy()
+        x = torch.zeros(int(co[-1]), dtype=torch.float64, device="cuda")
+        res = sme.sme_batch_lsqr(b, ub, vb, bcat, x, tol=1e-8, max_iters=5000, check_every=1)
+        x = x.cpu().numpy()
+    finally:
+        sme.sme_batch_destroy(b)
+    for i, A in enumerate(mats):
+        assert res[i]["converged"] == 1
+        xi = x[co[i]:co[i + 1]]
+        rel = np.linalg.norm(O.csr_matvec(A, xi) - bvecs[i]) / np.linalg.norm(bvecs[i])
+        assert rel <= 1e-8 and res[i]["rel_residual"] == pytest.approx(rel, rel=1e-6)
+        op, dt = make_op(A)
+        try:
+            args = (torch.tensor(st[2][ro[i]:ro[i + 1]], device="cuda"), torch.tensor(st[3][co[i]:co[i + 1]], device="cuda"),
+                    torch.tensor(bvecs[i], device="cuda"))
+            x1 = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+            sme.sme_lsqr(op, *args, x1, tol=0.0, max_iters=5, check_every=5)
+            np.testing.assert_allclose(x1.cpu().numpy(), x5[co[i]:co[i + 1]], rtol=1e-10,
+                                       atol=1e-12 * np.abs(x5[co[i]:co[i + 1]]).max())
+            x1.zero_()
+            r1 = sme.sme_lsqr(op, *args, x1, tol=1e-8, max_iters=5000, check_every=1)
+        finally:
+            sme.sme_op_destroy(op)
+        assert r1["converged"] == 1
+        assert abs(r1["iters"] - res[i]["iters"]) <= max(2, 0.02 * r1["iters"])
