@@ -165,6 +165,36 @@ sme_status sme_equilibrate(sme_op op, const sme_equil_params *p, void *u, void *
 sme_status sme_op_autotune(sme_op op, int32_t k, int32_t *slices_per_cta, int32_t *cols_first,
                            float *ms_per_iteration, void *stream);
 
+/*
+ * sme_equilibrate_targets -- Algorithm 1 for varying row and column norms (Section 6): the rows of DAE
+ * should have squared norms row_targets_sq[i] and the columns col_targets_sq[j] (device vectors in the
+ * state type, original order; the problem is consistent when their sums agree).  The gradient estimate
+ * becomes |DAE s|^2 - r + gamma u (and likewise for v); alpha and beta in p are ignored.  Sparse,
+ * single (non-batch) operators.  Otherwise as sme_equilibrate.
+ */
+sme_status sme_equilibrate_targets(sme_op op, const sme_equil_params *p, const void *row_targets_sq,
+                                   const void *col_targets_sq, void *u, void *v, void *u_bar, void *v_bar,
+                                   void *stream);
+
+/*
+ * sme_equilibrate_symmetric -- Algorithm 2 (symmetric equilibration, Section 6): D = E = diag(e^u) for a
+ * square symmetric A, one probe block s per iteration (Philox stream stream_base), estimate
+ * z = (1/k) sum_p |D A D s_p|^2 and the projected step of Algorithm 1 on u alone.  u[n], u_bar[n] in/out
+ * as in sme_equilibrate; alpha <= 0 selects 1.  A's symmetry is the caller's promise (not checked).
+ */
+sme_status sme_equilibrate_symmetric(sme_op op, const sme_equil_params *p, void *u, void *u_bar, void *stream);
+
+/*
+ * sme_equilibrate_block -- block equilibration (Section 6): rows in p_blocks contiguous blocks
+ * [row_block_ptr[b], row_block_ptr[b+1]) share the scaling e^{u_b}, columns in q_blocks blocks share
+ * e^{v_c} (HOST offset arrays of p_blocks+1 and q_blocks+1 entries, starting at 0 and ending at m / n).
+ * The block gradient is sum_{i in b} (|DAE|^2 1)_i - alpha^2 m_b + gamma u_b, estimated by summing the
+ * rows' estimates of the block.  u, u_bar hold p_blocks entries, v, v_bar q_blocks (device, state type).
+ */
+sme_status sme_equilibrate_block(sme_op op, const sme_equil_params *p, int64_t p_blocks,
+                                 const int64_t *row_block_ptr, int64_t q_blocks, const int64_t *col_block_ptr,
+                                 void *u, void *v, void *u_bar, void *v_bar, void *stream);
+
 /* sme_op_check -- synchronise `stream`, return and clear the op's device status word. */
 sme_status sme_op_check(sme_op op, void *stream);
 

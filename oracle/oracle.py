@@ -28,7 +28,8 @@ from .build import build_oracle
 
 __all__ = [
     "lib", "philox4x32_10", "probe_signs", "row_estimate", "col_estimate", "psgd_step", "equilibrate",
-    "psgd_step_sampled", "exact_norms_sq", "csr_matvec", "dense_estimate_sampled", "default_params", "objective", "gradient",
+    "psgd_step_sampled", "exact_norms_sq", "csr_matvec", "dense_estimate_sampled", "psgd_step_targets",
+    "psgd_step_symmetric", "block_step", "default_params", "objective", "gradient",
     "rms_error", "spread", "log_phi", "kappa", "sinkhorn_knopp", "block_minimize_u", "block_minimize_v",
     "regularized_optimum", "lsqr", "LsqrResult", "OracleCSR",
 ]
@@ -54,6 +55,11 @@ def lib():
         L.or_col_estimate.argtypes = est
         L.or_psgd_step.argtypes = [_i64, _i64, _i64p, _i32p, _dp, _d, _d, _d, _d, _i32, _i32, _dp, _dp, _i32,
                                    _dp, _dp, _dp, _dp]
+        L.or_psgd_step_targets.argtypes = [_i64, _i64, _i64p, _i32p, _dp, _dp, _dp, _d, _d, _d, _d, _i32, _i32, _dp,
+                                           _dp, _i32, _dp, _dp, _dp, _dp]
+        L.or_psgd_step_symmetric.argtypes = [_i64, _i64p, _i32p, _dp, _d, _d, _d, _i32, _i32, _dp, _i32, _dp, _dp]
+        L.or_block_step.argtypes = [_i64, _i64, _i64p, _i32p, _dp, _i64, _i64p, _i64, _i64p, _d, _d, _d, _d, _i32,
+                                    _i32, _dp, _dp, _i32, _dp, _dp, _dp, _dp]
         L.or_equilibrate.argtypes = [_i64, _i64, _i64p, _i32p, _dp, _d, _d, _d, _d, _i32, _i32, _i32, _i32, _u64,
                                      _i32, _dp, _dp, _dp, _dp]
         L.or_psgd_step_sampled.argtypes = [_i64, _i64, _i64p, _i32p, _dp, _d, _d, _d, _d, _i32, _i32, _i32, _u64,
@@ -168,6 +174,46 @@ def psgd_step(A, u, v, ubar, vbar, s, w, t, *, alpha, beta, gamma, M, t0=0):
                        alpha, beta, gamma, M, t, t0, _p(s, _dp), _p(w, _dp), k,
                        _p(u, _dp), _p(v, _dp), _p(ubar, _dp), _p(vbar, _dp))
     return u, v, ubar, vbar
+
+
+def psgd_step_targets(A, u, v, ubar, vbar, s, w, t, *, rt, ct, gamma, M, t0=0):
+    """One iteration t with squared target norms rt (rows) and ct (columns) (Section 6, varying norms)."""
+    A = _csr(A)
+    s = _f64(s).reshape(A.n, -1)
+    w = _f64(w).reshape(A.m, -1)
+    k = s.shape[1]
+    u, v, ubar, vbar = (_f64(x).copy() for x in (u, v, ubar, vbar))
+    rt, ct = _f64(rt), _f64(ct)
+    lib().or_psgd_step_targets(A.m, A.n, _p(A.row_ptr, _i64p), _p(A.col_idx, _i32p), _p(A.vals, _dp), _p(rt, _dp),
+                               _p(ct, _dp), 0.0, 0.0, gamma, M, t, t0, _p(s, _dp), _p(w, _dp), k,
+                               _p(u, _dp), _p(v, _dp), _p(ubar, _dp), _p(vbar, _dp))
+    return u, v, ubar, vbar
+
+
+def psgd_step_symmetric(A, u, ubar, s, t, *, alpha, gamma, M, t0=0):
+    """One iteration t of Algorithm 2 (D = E) with explicit signs s (n x k)."""
+    A = _csr(A)
+    s = _f64(s).reshape(A.n, -1)
+    k = s.shape[1]
+    u, ubar = _f64(u).copy(), _f64(ubar).copy()
+    lib().or_psgd_step_symmetric(A.n, _p(A.row_ptr, _i64p), _p(A.col_idx, _i32p), _p(A.vals, _dp), alpha, gamma, M,
+                                 t, t0, _p(s, _dp), k, _p(u, _dp), _p(ubar, _dp))
+    return u, ubar
+
+
+def block_step(A, rb, cb, ub, vb, ubb, vbb, s, w, t, *, alpha, beta, gamma, M, t0=0):
+    """One iteration t of block equilibration: row blocks rb (offsets, p+1), column blocks cb (q+1)."""
+    A = _csr(A)
+    s = _f64(s).reshape(A.n, -1)
+    w = _f64(w).reshape(A.m, -1)
+    k = s.shape[1]
+    rb = np.ascontiguousarray(rb, dtype=np.int64)
+    cb = np.ascontiguousarray(cb, dtype=np.int64)
+    ub, vb, ubb, vbb = (_f64(x).copy() for x in (ub, vb, ubb, vbb))
+    lib().or_block_step(A.m, A.n, _p(A.row_ptr, _i64p), _p(A.col_idx, _i32p), _p(A.vals, _dp), rb.size - 1,
+                        _p(rb, _i64p), cb.size - 1, _p(cb, _i64p), alpha, beta, gamma, M, t, t0, _p(s, _dp),
+                        _p(w, _dp), k, _p(ub, _dp), _p(vb, _dp), _p(ubb, _dp), _p(vbb, _dp))
+    return ub, vb, ubb, vbb
 
 
 def equilibrate(A, *, T: int, k: int, seed: int = 0, alpha=None, beta=None, gamma=None, M=None,

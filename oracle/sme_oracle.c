@@ -136,12 +136,14 @@ static double clip(double x, double lo, double hi)
     return x < lo ? lo : (x > hi ? hi : x);
 }
 
-/* One iteration t of Algorithm 1 with explicit probe signs s (n x k) and w (m x k).
+/* One iteration t of Algorithm 1 with explicit probe signs s (n x k) and w (m x k), and optional
+ * per-row / per-column squared target norms rt (m), ct (n) in place of alpha^2, beta^2 (the varying-norm
+ * variant of Section 6: gradient |DAE|^2 1 - r + gamma u).
  * u, v hold u^{t-1}, v^{t-1} on entry and u^t, v^t on exit; ubar, vbar are the running averages. */
-void or_psgd_step(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
-                  double alpha, double beta, double gamma, double M, int32_t t, int32_t t0,
-                  const double *s, const double *w, int32_t k,
-                  double *u, double *v, double *ubar, double *vbar)
+void or_psgd_step_targets(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                          const double *rt, const double *ct, double alpha, double beta, double gamma, double M,
+                          int32_t t, int32_t t0, const double *s, const double *w, int32_t k,
+                          double *u, double *v, double *ubar, double *vbar)
 {
     double *zu = (double *)malloc((size_t)m * sizeof(double));
     double *zv = (double *)malloc((size_t)n * sizeof(double));
@@ -149,15 +151,89 @@ void or_psgd_step(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *c
     or_col_estimate(m, n, row_ptr, col, val, u, v, w, k, zv);
     double eta = 2.0 / (gamma * ((double)t + (double)t0 + 1.0));
     for (int64_t i = 0; i < m; ++i) {
-        double un = clip(u[i] - eta * (zu[i] - alpha * alpha + gamma * u[i]), -M, M);
+        double target = rt ? rt[i] : alpha * alpha;
+        double un = clip(u[i] - eta * (zu[i] - target + gamma * u[i]), -M, M);
         u[i] = un;
         ubar[i] = 2.0 * un / ((double)t + 2.0) + (double)t * ubar[i] / ((double)t + 2.0);
     }
     for (int64_t j = 0; j < n; ++j) {
-        double vn = clip(v[j] - eta * (zv[j] - beta * beta + gamma * v[j]), -M, M);
+        double target = ct ? ct[j] : beta * beta;
+        double vn = clip(v[j] - eta * (zv[j] - target + gamma * v[j]), -M, M);
         v[j] = vn;
         vbar[j] = 2.0 * vn / ((double)t + 2.0) + (double)t * vbar[j] / ((double)t + 2.0);
     }
+    free(zu);
+    free(zv);
+}
+
+void or_psgd_step(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                  double alpha, double beta, double gamma, double M, int32_t t, int32_t t0,
+                  const double *s, const double *w, int32_t k,
+                  double *u, double *v, double *ubar, double *vbar)
+{
+    or_psgd_step_targets(m, n, row_ptr, col, val, NULL, NULL, alpha, beta, gamma, M, t, t0, s, w, k, u, v, ubar,
+                         vbar);
+}
+
+/* One iteration t of Algorithm 2 (symmetric equilibration, Section 6): D = E = diag(e^u),
+ * z_i = (1/k) sum_p ((D A D s_p)_i)^2 with signs s (n x k), then the projected step and the average. */
+void or_psgd_step_symmetric(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                            double alpha, double gamma, double M, int32_t t, int32_t t0, const double *s, int32_t k,
+                            double *u, double *ubar)
+{
+    double *z = (double *)malloc((size_t)n * sizeof(double));
+    or_row_estimate(n, n, row_ptr, col, val, u, u, s, k, z);
+    double eta = 2.0 / (gamma * ((double)t + (double)t0 + 1.0));
+    for (int64_t i = 0; i < n; ++i) {
+        double un = clip(u[i] - eta * (z[i] - alpha * alpha + gamma * u[i]), -M, M);
+        u[i] = un;
+        ubar[i] = 2.0 * un / ((double)t + 2.0) + (double)t * ubar[i] / ((double)t + 2.0);
+    }
+    free(z);
+}
+
+/* One iteration t of block equilibration (Section 6): rows split into p contiguous blocks
+ * [rb[b], rb[b+1]) sharing the scaling e^{ub[b]}, columns into q blocks [cb[c], cb[c+1]) sharing e^{vb[c]}.
+ * The block gradient is sum_{i in b} (|DAE|^2 1)_i - alpha^2 m_b + gamma u_b; its estimate sums the row
+ * estimates of the block.  ub, vb (block iterates) and ubb, vbb (block averages) are updated. */
+void or_block_step(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                   int64_t p, const int64_t *rb, int64_t q, const int64_t *cb, double alpha, double beta,
+                   double gamma, double M, int32_t t, int32_t t0, const double *s, const double *w, int32_t k,
+                   double *ub, double *vb, double *ubb, double *vbb)
+{
+    double *u = (double *)malloc((size_t)m * sizeof(double));
+    double *v = (double *)malloc((size_t)n * sizeof(double));
+    for (int64_t b = 0; b < p; ++b)
+        for (int64_t i = rb[b]; i < rb[b + 1]; ++i)
+            u[i] = ub[b];
+    for (int64_t c = 0; c < q; ++c)
+        for (int64_t j = cb[c]; j < cb[c + 1]; ++j)
+            v[j] = vb[c];
+    double *zu = (double *)malloc((size_t)m * sizeof(double));
+    double *zv = (double *)malloc((size_t)n * sizeof(double));
+    or_row_estimate(m, n, row_ptr, col, val, u, v, s, k, zu);
+    or_col_estimate(m, n, row_ptr, col, val, u, v, w, k, zv);
+    double eta = 2.0 / (gamma * ((double)t + (double)t0 + 1.0));
+    for (int64_t b = 0; b < p; ++b) {
+        double zb = 0.0;
+        for (int64_t i = rb[b]; i < rb[b + 1]; ++i)
+            zb += zu[i];
+        double mb = (double)(rb[b + 1] - rb[b]);
+        double un = clip(ub[b] - eta * (zb - alpha * alpha * mb + gamma * ub[b]), -M, M);
+        ub[b] = un;
+        ubb[b] = 2.0 * un / ((double)t + 2.0) + (double)t * ubb[b] / ((double)t + 2.0);
+    }
+    for (int64_t c = 0; c < q; ++c) {
+        double zc = 0.0;
+        for (int64_t j = cb[c]; j < cb[c + 1]; ++j)
+            zc += zv[j];
+        double nc = (double)(cb[c + 1] - cb[c]);
+        double vn = clip(vb[c] - eta * (zc - beta * beta * nc + gamma * vb[c]), -M, M);
+        vb[c] = vn;
+        vbb[c] = 2.0 * vn / ((double)t + 2.0) + (double)t * vbb[c] / ((double)t + 2.0);
+    }
+    free(u);
+    free(v);
     free(zu);
     free(zv);
 }

@@ -126,7 +126,8 @@ extern "C" sme_status sme_op_destroy(sme_op op)
     free_sell(op, op->fwd);
     free_sell(op, op->bwd);
     Workspace &W = op->ws;
-    for (void *p : {W.u, W.v, W.ub, W.vb, W.tab_u[0], W.tab_u[1], W.tab_v[0], W.tab_v[1], (void *)W.red})
+    for (void *p : {W.u, W.v, W.ub, W.vb, W.tab_u[0], W.tab_u[1], W.tab_v[0], W.tab_v[1], (void *)W.red, W.tgt[0],
+                    W.tgt[1], (void *)W.sym_pos})
         if (p) cudaFree(p);
     release_lsqr(op);
     if (op->graph.exec) cudaGraphExecDestroy(op->graph.exec);

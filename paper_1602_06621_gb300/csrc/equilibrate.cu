@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "sme_internal.cuh"
 
@@ -55,6 +56,10 @@ struct StepArgs {
     const int32_t *loc[2];
     const real *tgt2[2];
     uint32_t sid_base;
+    // Varying norms: squared targets per sorted row [0] / column [1], or null.
+    const real *tgt_row[2];
+    // Symmetric equilibration (mode 2): sorted column position of each sorted row's index.
+    const int32_t *sym_pos;
 };
 
 // ------------------------------------------------------------------ gather tables
@@ -283,6 +288,8 @@ __global__ void __launch_bounds__(SPC * 32) sgd_iteration(StepArgs<real> a)
         pidx = (uint32_t)(cols ? a.loc[1] : a.loc[0])[r];
         psid = a.sid_base + 2u * (uint32_t)b + (cols ? 0u : 1u);
     }
+    const real *TR = cols ? a.tgt_row[1] : a.tgt_row[0];
+    if (TR) t2 = TR[r];
     real xn = xo - a.eta * (z - t2 + a.gamma * xo);
     if (!isfinite(xn)) atomicOr(a.status, ST_NONFINITE);
     xn = dclip(xn, a.M);
@@ -290,6 +297,12 @@ __global__ void __launch_bounds__(SPC * 32) sgd_iteration(StepArgs<real> a)
     real *XB = cols ? a.xb[1] : a.xb[0];
     XB[r] = a.avg_new * xn + a.avg_old * XB[r];
     uint32_t pw0, pw1;
+    if (a.mode == 2) {
+        // Symmetric: D = E, so the new e^{u_i} and the s-probes of index i feed the column table.
+        probe_words2(pidx, a.t_next, a.sid_out[1], a.key0, a.key1, pw0, pw1);
+        Tab::store(a.tab_out[1], a.sym_pos[r], dexp(xn), pw0, pw1);
+        return;
+    }
     probe_words2(pidx, a.t_next, psid, a.key0, a.key1, pw0, pw1);
     Tab::store(cols ? a.tab_out[1] : a.tab_out[0], r, dexp(xn), pw0, pw1);
 }
@@ -509,6 +522,10 @@ static StepArgs<real> base_args(sme_op op, int buf_in, const Resolved &R, uint64
         }
         a.sid_base = op->batch->sid_base;
     }
+    if (op->ws.use_tgt) {
+        a.tgt_row[0] = (const real *)op->ws.tgt[0];
+        a.tgt_row[1] = (const real *)op->ws.tgt[1];
+    }
     return a;
 }
 
@@ -556,7 +573,8 @@ static sme_status equilibrate_t(sme_op op, const sme_equil_params *p, real *u, r
         // so one captured graph is replayed for repeated calls with the same parameters.
         const int64_t key[12] = {p->T, p->k, p->t_begin, p->t0, (int64_t)p->seed, p->stream_base,
                                  (int64_t)(R.alpha * 1e15), (int64_t)(R.beta * 1e15), (int64_t)(R.gamma * 1e15),
-                                 (int64_t)(R.M * 1e15), (int64_t)op->ws.tab_bytes_u, sh.spc * 2 + sh.cols_first};
+                                 (int64_t)(R.M * 1e15), (int64_t)op->ws.tab_bytes_u,
+                                 sh.spc * 4 + sh.cols_first * 2 + (op->ws.use_tgt ? 1 : 0)};
         GraphCache &G = op->graph;
         if (!G.exec || std::memcmp(G.key, key, sizeof(key)) != 0) {
             if (G.exec) {
@@ -608,6 +626,153 @@ static sme_status estimate_t(sme_op op, const real *u, const real *v, int t, int
     if (!zv) a.A[1].nslices = 0;
     launch_iteration<real>(a, k, sh.spc, grid_for(op, sh), s);
     SME_CUDA(cudaGetLastError());
+    return SME_OK;
+}
+
+// Squared targets in sorted order: out[r] = in[perm[r]].
+template <typename real>
+__global__ void permute_in(int64_t n, const int32_t *perm, const real *in, real *out)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) out[r] = in[perm[r]];
+}
+
+__global__ void sym_positions(int64_t n, const int32_t *perm_r, const int32_t *iperm_c, int32_t *pos)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) pos[r] = iperm_c[perm_r[r]];
+}
+
+template <typename real>
+static sme_status targets_t(sme_op op, const sme_equil_params *p, const real *rt, const real *ct, real *u, real *v,
+                            real *ub, real *vb, cudaStream_t s)
+{
+    Workspace &W = op->ws;
+    const size_t sz = op->dbl ? 8 : 4;
+    if (!W.tgt[0]) {
+        SME_TRY(dev_alloc(op, &W.tgt[0], op->m * sz));
+        SME_TRY(dev_alloc(op, &W.tgt[1], op->n * sz));
+    }
+    permute_in<real><<<nblk(op->m), 256, 0, s>>>(op->m, op->fwd.perm, rt, (real *)W.tgt[0]);
+    permute_in<real><<<nblk(op->n), 256, 0, s>>>(op->n, op->bwd.perm, ct, (real *)W.tgt[1]);
+    W.use_tgt = true;
+    sme_status st = equilibrate_t<real>(op, p, u, v, ub, vb, s);
+    W.use_tgt = false;
+    return st;
+}
+
+template <typename real>
+static sme_status symmetric_t(sme_op op, const sme_equil_params *p, real *u, real *ub, cudaStream_t s)
+{
+    const int k = p->k, kw = (k + 31) / 32;
+    SME_TRY(ensure_equil_workspace(op, kw));
+    Workspace &W = op->ws;
+    if (!W.sym_pos) {
+        SME_TRY(dev_alloc(op, (void **)&W.sym_pos, op->m * sizeof(int32_t)));
+        sym_positions<<<nblk(op->m), 256, 0, s>>>(op->m, op->fwd.perm, op->bwd.iperm, W.sym_pos);
+    }
+    const Resolved R = resolve(op, p->alpha, p->alpha, p->gamma, p->M);
+    const uint32_t sid_s = (uint32_t)p->stream_base;
+    const int tb = p->t_begin;
+    const int buf = tb & 1;
+    launch_load<real>(op, 0, kw, u, ub, (real *)W.u, (real *)W.ub, W.tab_u[buf], (uint32_t)tb, sid_s + 1u, p->seed, s);
+    launch_load<real>(op, 1, kw, u, nullptr, (real *)W.v, nullptr, W.tab_v[buf], (uint32_t)tb, sid_s, p->seed, s);
+    Shape sh;  // rows only: the default shape
+    const unsigned grid = (unsigned)((op->fwd.nslices + sh.spc - 1) / sh.spc);
+    for (int t = tb; t < tb + p->T; ++t) {
+        StepArgs<real> a = base_args<real>(op, t & 1, R, p->seed, sh);
+        a.eta = (real)(2.0 / (R.gamma * ((double)t + (double)p->t0 + 1.0)));
+        a.avg_new = (real)(2.0 / ((double)t + 2.0));
+        a.avg_old = (real)((double)t / ((double)t + 2.0));
+        a.t_next = (uint32_t)(t + 1);
+        a.sid_out[0] = sid_s + 1u;
+        a.sid_out[1] = sid_s;
+        a.mode = 2;
+        a.sym_pos = W.sym_pos;
+        a.A[1].nslices = 0;
+        launch_iteration<real>(a, k, sh.spc, grid, s);
+    }
+    store_state<real><<<nblk(op->m), 256, 0, s>>>(op->m, op->fwd.perm, (real *)W.u, (real *)W.ub, u, ub);
+    SME_CUDA(cudaGetLastError());
+    return SME_OK;
+}
+
+// Block equilibration: expand block scalings to rows / columns (original order).
+template <typename real>
+__global__ void expand_blocks(int64_t n, const int32_t *blk, const real *xb, real *x)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = xb[blk[i]];
+}
+
+// One CTA per block: z_b = sum of the block's estimates (FP64, fixed order), then the projected step and
+// the running average of the block variable.  Row blocks first, then column blocks.
+template <typename real>
+__global__ void block_step_kernel(int64_t p, const int64_t *rb, int64_t q, const int64_t *cb, const real *zu,
+                                  const real *zv, real *ub, real *vb, real *ubb, real *vbb, double a2, double b2,
+                                  double gamma, double M, double eta, double avg_new, double avg_old, int *status)
+{
+    __shared__ double sh[256];
+    const int64_t g = blockIdx.x;
+    const bool colb = g >= p;
+    const int64_t b = colb ? g - p : g;
+    const int64_t lo = colb ? cb[b] : rb[b], hi = colb ? cb[b + 1] : rb[b + 1];
+    const real *z = colb ? zv : zu;
+    double acc = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += (double)z[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    real *X = colb ? vb : ub, *XB = colb ? vbb : ubb;
+    const double xo = (double)X[b];
+    const double target = (colb ? b2 : a2) * (double)(hi - lo);
+    double xn = xo - eta * (sh[0] - target + gamma * xo);
+    if (!isfinite(xn)) atomicOr(status, ST_NONFINITE);
+    xn = fmin(fmax(xn, -M), M);
+    X[b] = (real)xn;
+    XB[b] = (real)(avg_new * xn + avg_old * (double)XB[b]);
+}
+
+template <typename real>
+static sme_status block_t(sme_op op, const sme_equil_params *p, int64_t pb, const int64_t *rb_h, int64_t qb,
+                          const int64_t *cb_h, real *ub, real *vb, real *ubb, real *vbb, cudaStream_t s)
+{
+    const int k = p->k;
+    const Resolved R = resolve(op, p->alpha, p->beta, p->gamma, p->M);
+    const int64_t m = op->m, n = op->n;
+    std::vector<int32_t> br(m), bc(n);
+    for (int64_t b = 0; b < pb; ++b)
+        for (int64_t i = rb_h[b]; i < rb_h[b + 1]; ++i) br[i] = (int32_t)b;
+    for (int64_t c = 0; c < qb; ++c)
+        for (int64_t j = cb_h[c]; j < cb_h[c + 1]; ++j) bc[j] = (int32_t)c;
+    const size_t sz = sizeof(real);
+    char *buf = nullptr;
+    const size_t bytes = (size_t)(m + n) * 4 + (size_t)(pb + qb + 2) * 8 + (size_t)2 * (m + n) * sz;
+    SME_CUDA(cudaMallocAsync((void **)&buf, bytes, s));
+    int32_t *dbr = (int32_t *)buf, *dbc = dbr + m;
+    int64_t *drb = (int64_t *)(buf + (size_t)(m + n) * 4), *dcb = drb + pb + 1;
+    real *xr = (real *)(buf + (size_t)(m + n) * 4 + (size_t)(pb + qb + 2) * 8), *xc = xr + m, *zu = xc + n,
+         *zv = zu + m;
+    SME_CUDA(cudaMemcpyAsync(dbr, br.data(), m * 4, cudaMemcpyHostToDevice, s));
+    SME_CUDA(cudaMemcpyAsync(dbc, bc.data(), n * 4, cudaMemcpyHostToDevice, s));
+    SME_CUDA(cudaMemcpyAsync(drb, rb_h, (pb + 1) * 8, cudaMemcpyHostToDevice, s));
+    SME_CUDA(cudaMemcpyAsync(dcb, cb_h, (qb + 1) * 8, cudaMemcpyHostToDevice, s));
+    for (int t = p->t_begin; t < p->t_begin + p->T; ++t) {
+        expand_blocks<real><<<nblk(m), 256, 0, s>>>(m, dbr, ub, xr);
+        expand_blocks<real><<<nblk(n), 256, 0, s>>>(n, dbc, vb, xc);
+        SME_TRY(estimate_t<real>(op, xr, xc, t, k, p->seed, p->stream_base, zu, zv, s));
+        const double eta = 2.0 / (R.gamma * ((double)t + (double)p->t0 + 1.0));
+        block_step_kernel<real><<<(unsigned)(pb + qb), 256, 0, s>>>(pb, drb, qb, dcb, zu, zv, ub, vb, ubb, vbb,
+                                                                   R.alpha * R.alpha, R.beta * R.beta, R.gamma, R.M,
+                                                                   eta, 2.0 / ((double)t + 2.0),
+                                                                   (double)t / ((double)t + 2.0), op->d_status);
+    }
+    SME_CUDA(cudaGetLastError());
+    SME_CUDA(cudaFreeAsync(buf, s));
     return SME_OK;
 }
 
@@ -729,6 +894,90 @@ extern "C" sme_status sme_equilibrate(sme_op op, const sme_equil_params *p, void
         SME_TRY(equilibrate_t<float>(op, p, (float *)u, (float *)v, (float *)u_bar, (float *)v_bar,
                                      (cudaStream_t)stream));
     }
+    if (p->flags & SME_EQ_ASYNC) return SME_OK;
+    return sme_op_check(op, stream);
+}
+
+extern "C" sme_status sme_equilibrate_targets(sme_op op, const sme_equil_params *p, const void *row_targets_sq,
+                                              const void *col_targets_sq, void *u, void *v, void *u_bar,
+                                              void *v_bar, void *stream)
+{
+    if (!op || !p || !row_targets_sq || !col_targets_sq || !u || !v || !u_bar || !v_bar || p->T < 0 ||
+        p->t_begin < 1 || p->t0 < 0 || op->dense || op->batch) {
+        set_error("sme_equilibrate_targets: bad arguments (sparse single operators only)");
+        return SME_ERR_ARG;
+    }
+    if (!k_supported(p->k)) {
+        set_error("sme_equilibrate_targets: k=%d not supported", p->k);
+        return SME_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (op->dbl)
+        SME_TRY(targets_t<double>(op, p, (const double *)row_targets_sq, (const double *)col_targets_sq, (double *)u,
+                                  (double *)v, (double *)u_bar, (double *)v_bar, s));
+    else
+        SME_TRY(targets_t<float>(op, p, (const float *)row_targets_sq, (const float *)col_targets_sq, (float *)u,
+                                 (float *)v, (float *)u_bar, (float *)v_bar, s));
+    if (p->flags & SME_EQ_ASYNC) return SME_OK;
+    return sme_op_check(op, stream);
+}
+
+extern "C" sme_status sme_equilibrate_symmetric(sme_op op, const sme_equil_params *p, void *u, void *u_bar,
+                                                void *stream)
+{
+    if (!op || !p || !u || !u_bar || p->T < 0 || p->t_begin < 1 || p->t0 < 0 || op->dense || op->batch ||
+        op->m != op->n) {
+        set_error("sme_equilibrate_symmetric: bad arguments (square sparse single operators only)");
+        return SME_ERR_ARG;
+    }
+    if (!k_supported(p->k)) {
+        set_error("sme_equilibrate_symmetric: k=%d not supported", p->k);
+        return SME_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (op->dbl)
+        SME_TRY(symmetric_t<double>(op, p, (double *)u, (double *)u_bar, s));
+    else
+        SME_TRY(symmetric_t<float>(op, p, (float *)u, (float *)u_bar, s));
+    if (p->flags & SME_EQ_ASYNC) return SME_OK;
+    return sme_op_check(op, stream);
+}
+
+extern "C" sme_status sme_equilibrate_block(sme_op op, const sme_equil_params *p, int64_t p_blocks,
+                                            const int64_t *row_block_ptr, int64_t q_blocks,
+                                            const int64_t *col_block_ptr, void *u, void *v, void *u_bar,
+                                            void *v_bar, void *stream)
+{
+    if (!op || !p || !row_block_ptr || !col_block_ptr || !u || !v || !u_bar || !v_bar || p->T < 0 ||
+        p->t_begin < 1 || p->t0 < 0 || op->dense || op->batch || p_blocks < 1 || q_blocks < 1) {
+        set_error("sme_equilibrate_block: bad arguments (sparse single operators only)");
+        return SME_ERR_ARG;
+    }
+    const int64_t lim[2] = {op->m, op->n};
+    const int64_t *ptr[2] = {row_block_ptr, col_block_ptr};
+    const int64_t cnt[2] = {p_blocks, q_blocks};
+    for (int side = 0; side < 2; ++side) {
+        if (ptr[side][0] != 0 || ptr[side][cnt[side]] != lim[side]) {
+            set_error("sme_equilibrate_block: block offsets must run from 0 to the dimension");
+            return SME_ERR_ARG;
+        }
+        for (int64_t b = 0; b < cnt[side]; ++b)
+            if (ptr[side][b + 1] <= ptr[side][b]) {
+                set_error("sme_equilibrate_block: empty or decreasing block");
+                return SME_ERR_ARG;
+            }
+    }
+    if (!k_supported(p->k)) {
+        set_error("sme_equilibrate_block: k=%d not supported", p->k);
+        return SME_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (op->dbl)
+        SME_TRY(block_t<double>(op, p, p_blocks, row_block_ptr, q_blocks, col_block_ptr, (double *)u, (double *)v,
+                                (double *)u_bar, (double *)v_bar, s));
+    else
+        SME_TRY(block_t<float>(op, p, p_blocks, row_block_ptr, q_blocks, col_block_ptr, (float *)u, (float *)v,
+                               (float *)u_bar, (float *)v_bar, s));
     if (p->flags & SME_EQ_ASYNC) return SME_OK;
     return sme_op_check(op, stream);
 }

@@ -111,6 +111,10 @@ struct Workspace {
     int64_t lsqr_bytes = 0;
     double *red = nullptr;
     int64_t red_len = 0;
+    // Varying-norm targets (sorted order) and the symmetric row -> column map.
+    void *tgt[2] = {nullptr, nullptr};
+    bool use_tgt = false;
+    int32_t *sym_pos = nullptr;
 };
 
 struct GraphCache {

@@ -20,6 +20,7 @@ __all__ = [
     "sme_equilibrate", "sme_op_check", "sme_estimate", "sme_evaluate", "sme_lsqr", "sme_status_string",
     "default_params", "sme_estimate_rows_static", "SME_STATIC_MAX_COLS", "sme_batch_create", "sme_batch_destroy",
     "sme_batch_get_info", "sme_batch_equilibrate", "sme_batch_estimate", "sme_batch_op", "sme_op_autotune", "sme_batch_lsqr",
+    "sme_equilibrate_targets", "sme_equilibrate_symmetric", "sme_equilibrate_block",
 ]
 SME_STATIC_MAX_COLS = 1 << 20
 
@@ -93,6 +94,10 @@ SIGNATURES = {
     "sme_op_autotune": ([_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float), _vp],
                         _i32),
     "sme_batch_lsqr": ([_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(sme_lsqr_params), _vp, _vp], _i32),
+    "sme_equilibrate_targets": ([_vp, ctypes.POINTER(sme_equil_params), _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
+    "sme_equilibrate_symmetric": ([_vp, ctypes.POINTER(sme_equil_params), _vp, _vp, _vp], _i32),
+    "sme_equilibrate_block": ([_vp, ctypes.POINTER(sme_equil_params), _i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp],
+                              _i32),
 }
 
 
@@ -310,3 +315,32 @@ def sme_batch_lsqr(b, u_bar, v_bar, bvec, x, *, tol=1e-6, max_iters=100000, chec
     if st != -7 or raise_on_not_converged:
         _check(st, "sme_batch_lsqr")
     return [{f: getattr(r, f) for f, _ in sme_lsqr_result._fields_} for r in res]
+
+
+def _params(T, k, t_begin, t0, seed, stream_base, alpha, beta, gamma, M, flags):
+    return sme_equil_params(alpha, beta, gamma, M, int(T), int(k), int(t_begin), int(t0), int(seed), int(stream_base),
+                            int(flags))
+
+
+def sme_equilibrate_targets(op, row_targets_sq, col_targets_sq, u, v, u_bar, v_bar, *, T, k, t_begin=1, t0=0, seed=0,
+                            stream_base=0, gamma=0.0, M=0.0, flags=0, stream=None):
+    p = _params(T, k, t_begin, t0, seed, stream_base, 0.0, 0.0, gamma, M, flags)
+    _check(load().sme_equilibrate_targets(op, ctypes.byref(p), _ptr(row_targets_sq), _ptr(col_targets_sq), _ptr(u),
+                                          _ptr(v), _ptr(u_bar), _ptr(v_bar), _stream(stream)),
+           "sme_equilibrate_targets")
+
+
+def sme_equilibrate_symmetric(op, u, u_bar, *, T, k, t_begin=1, t0=0, seed=0, stream_base=0, alpha=0.0, gamma=0.0,
+                              M=0.0, flags=0, stream=None):
+    p = _params(T, k, t_begin, t0, seed, stream_base, alpha, alpha, gamma, M, flags)
+    _check(load().sme_equilibrate_symmetric(op, ctypes.byref(p), _ptr(u), _ptr(u_bar), _stream(stream)),
+           "sme_equilibrate_symmetric")
+
+
+def sme_equilibrate_block(op, row_block_ptr, col_block_ptr, u, v, u_bar, v_bar, *, T, k, t_begin=1, t0=0, seed=0,
+                          stream_base=0, alpha=0.0, beta=0.0, gamma=0.0, M=0.0, flags=0, stream=None):
+    rb = np.ascontiguousarray(row_block_ptr, dtype=np.int64)
+    cb = np.ascontiguousarray(col_block_ptr, dtype=np.int64)
+    p = _params(T, k, t_begin, t0, seed, stream_base, alpha, beta, gamma, M, flags)
+    _check(load().sme_equilibrate_block(op, ctypes.byref(p), rb.size - 1, _ptr(rb), cb.size - 1, _ptr(cb), _ptr(u),
+                                        _ptr(v), _ptr(u_bar), _ptr(v_bar), _stream(stream)), "sme_equilibrate_block")
