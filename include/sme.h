@@ -309,6 +309,44 @@ sme_status sme_batch_lsqr(sme_batch b, const void *u_bar, const void *v_bar, con
  * of all matrices at once (row / column norms come back concatenated). */
 sme_status sme_batch_op(sme_batch b, sme_op *op);
 
+/* ------------------------------------------------------------------ learned warm start */
+
+/*
+ * A small MLP that predicts initial log-scalings u^0, v^0 from per-row / per-column features, so that
+ * Algorithm 1 can start near its optimum.  The paper has no such component; it uses the paper's method
+ * unchanged.  Because the paper's first step eta_1 = 1/gamma discards u^0 (u^1 depends on u^0 only
+ * through the estimate), a warm start is used with a step offset t0 > 0 in sme_equil_params.
+ *
+ * Network: 8 normalised features -> 128 (ReLU) -> 128 (ReLU) -> 1, BF16 weights for the forward pass,
+ * FP32 master weights and FP32 accumulation, trained on the device by sme_mlp_train_step (mean squared
+ * error, Adam).  Features of row i (column j), see sme_op_features:
+ *   [ 1/2 log of the k = 8 sketch of the squared norm (sme_estimate at u = v = 0, t = 1),
+ *     log(1 + nonzeros), log(mean |A_ij|), side (0 rows, 1 columns),
+ *     mean sketch log-norm of the rows, of the columns, log m, log n ].
+ */
+typedef struct sme_mlp_s *sme_mlp;
+
+sme_status sme_mlp_create(sme_mlp *out, uint64_t seed);  /* He initialisation from `seed` */
+sme_status sme_mlp_destroy(sme_mlp mlp);
+int64_t sme_mlp_param_count(void);
+/* Host copies of the FP32 parameters (sme_mlp_param_count floats) and of the input normalisation
+ * (8 means then 8 scales); either pointer may be NULL.  set_params synchronises the device. */
+sme_status sme_mlp_get_params(sme_mlp mlp, float *params, float *norm);
+sme_status sme_mlp_set_params(sme_mlp mlp, const float *params, const float *norm);
+/* y[i] = MLP(X[i, :]) for X a device float array N x 8 (row-major). */
+sme_status sme_mlp_forward(sme_mlp mlp, const float *X, int64_t N, float *y, void *stream);
+/* Gradient of (1/N) sum_i (MLP(X_i) - target_i)^2 with respect to the parameters (device grad, may be
+ * NULL) and the loss (host, may be NULL; synchronises when given).  Deterministic. */
+sme_status sme_mlp_gradient(sme_mlp mlp, const float *X, const float *target, int64_t N, float *grad,
+                            float *loss, void *stream);
+/* One Adam step (beta1 0.9, beta2 0.999) on the same loss with learning rate lr. */
+sme_status sme_mlp_train_step(sme_mlp mlp, const float *X, const float *target, int64_t N, float lr, float *loss,
+                              void *stream);
+/* Features of every row (m x 8) and column (n x 8) of a sparse operator, device float arrays. */
+sme_status sme_op_features(sme_op op, uint64_t seed, float *row_features, float *col_features, void *stream);
+/* u0[m], v0[n] (state type) = the MLP's prediction for every row and column of `op`. */
+sme_status sme_warm_start(sme_op op, sme_mlp mlp, uint64_t seed, void *u0, void *v0, void *stream);
+
 /* ------------------------------------------------------------------ allocation-free estimator */
 
 /*

@@ -20,7 +20,9 @@ __all__ = [
     "sme_equilibrate", "sme_op_check", "sme_estimate", "sme_evaluate", "sme_lsqr", "sme_status_string",
     "default_params", "sme_estimate_rows_static", "SME_STATIC_MAX_COLS", "sme_batch_create", "sme_batch_destroy",
     "sme_batch_get_info", "sme_batch_equilibrate", "sme_batch_estimate", "sme_batch_op", "sme_op_autotune", "sme_batch_lsqr",
-    "sme_equilibrate_targets", "sme_equilibrate_symmetric", "sme_equilibrate_block",
+    "sme_equilibrate_targets", "sme_equilibrate_symmetric", "sme_equilibrate_block", "sme_mlp_create",
+    "sme_mlp_destroy", "sme_mlp_param_count", "sme_mlp_get_params", "sme_mlp_set_params", "sme_mlp_forward",
+    "sme_mlp_gradient", "sme_mlp_train_step", "sme_op_features", "sme_warm_start",
 ]
 SME_STATIC_MAX_COLS = 1 << 20
 
@@ -98,6 +100,16 @@ SIGNATURES = {
     "sme_equilibrate_symmetric": ([_vp, ctypes.POINTER(sme_equil_params), _vp, _vp, _vp], _i32),
     "sme_equilibrate_block": ([_vp, ctypes.POINTER(sme_equil_params), _i64, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp],
                               _i32),
+    "sme_mlp_create": ([ctypes.POINTER(_vp), _u64], _i32),
+    "sme_mlp_destroy": ([_vp], _i32),
+    "sme_mlp_param_count": ([], _i64),
+    "sme_mlp_get_params": ([_vp, _vp, _vp], _i32),
+    "sme_mlp_set_params": ([_vp, _vp, _vp], _i32),
+    "sme_mlp_forward": ([_vp, _vp, _i64, _vp, _vp], _i32),
+    "sme_mlp_gradient": ([_vp, _vp, _vp, _i64, _vp, _vp, _vp], _i32),
+    "sme_mlp_train_step": ([_vp, _vp, _vp, _i64, ctypes.c_float, _vp, _vp], _i32),
+    "sme_op_features": ([_vp, _u64, _vp, _vp, _vp], _i32),
+    "sme_warm_start": ([_vp, _vp, _u64, _vp, _vp, _vp], _i32),
 }
 
 
@@ -344,3 +356,58 @@ def sme_equilibrate_block(op, row_block_ptr, col_block_ptr, u, v, u_bar, v_bar, 
     p = _params(T, k, t_begin, t0, seed, stream_base, alpha, beta, gamma, M, flags)
     _check(load().sme_equilibrate_block(op, ctypes.byref(p), rb.size - 1, _ptr(rb), cb.size - 1, _ptr(cb), _ptr(u),
                                         _ptr(v), _ptr(u_bar), _ptr(v_bar), _stream(stream)), "sme_equilibrate_block")
+
+
+def sme_mlp_create(seed=0):
+    h = ctypes.c_void_p()
+    _check(load().sme_mlp_create(ctypes.byref(h), int(seed)), "sme_mlp_create")
+    return h
+
+
+def sme_mlp_destroy(mlp):
+    if mlp:
+        _check(load().sme_mlp_destroy(mlp), "sme_mlp_destroy")
+
+
+def sme_mlp_param_count() -> int:
+    return int(load().sme_mlp_param_count())
+
+
+def sme_mlp_get_params(mlp):
+    p = np.zeros(sme_mlp_param_count(), np.float32)
+    nrm = np.zeros(16, np.float32)
+    _check(load().sme_mlp_get_params(mlp, _ptr(p), _ptr(nrm)), "sme_mlp_get_params")
+    return p, nrm
+
+
+def sme_mlp_set_params(mlp, params=None, norm=None):
+    p = None if params is None else np.ascontiguousarray(params, np.float32)
+    nrm = None if norm is None else np.ascontiguousarray(norm, np.float32)
+    _check(load().sme_mlp_set_params(mlp, _ptr(p), _ptr(nrm)), "sme_mlp_set_params")
+
+
+def sme_mlp_forward(mlp, X, y, stream=None):
+    _check(load().sme_mlp_forward(mlp, _ptr(X), int(X.shape[0]), _ptr(y), _stream(stream)), "sme_mlp_forward")
+
+
+def sme_mlp_gradient(mlp, X, target, grad=None, stream=None):
+    loss = ctypes.c_float()
+    _check(load().sme_mlp_gradient(mlp, _ptr(X), _ptr(target), int(X.shape[0]), _ptr(grad), ctypes.byref(loss),
+                                   _stream(stream)), "sme_mlp_gradient")
+    return loss.value
+
+
+def sme_mlp_train_step(mlp, X, target, lr, stream=None, want_loss=False):
+    loss = ctypes.c_float()
+    _check(load().sme_mlp_train_step(mlp, _ptr(X), _ptr(target), int(X.shape[0]), float(lr),
+                                     ctypes.byref(loss) if want_loss else None, _stream(stream)), "sme_mlp_train_step")
+    return loss.value if want_loss else None
+
+
+def sme_op_features(op, seed, row_features, col_features, stream=None):
+    _check(load().sme_op_features(op, int(seed), _ptr(row_features), _ptr(col_features), _stream(stream)),
+           "sme_op_features")
+
+
+def sme_warm_start(op, mlp, seed, u0, v0, stream=None):
+    _check(load().sme_warm_start(op, mlp, int(seed), _ptr(u0), _ptr(v0), _stream(stream)), "sme_warm_start")

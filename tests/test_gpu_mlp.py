@@ -1,0 +1,182 @@
+"""The learned warm start on the GPU: the MLP kernels against the FP64 oracle (oracle/mlp.py), the feature
+kernel against the oracle's estimator, and the warm start's effect on Algorithm 1."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle import mlp as OM
+from paper_1602_06621_gb300 import inputs as I
+from paper_1602_06621_gb300 import sme as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(p):
+    """FP32 -> BF16 round to nearest even, as the device's copies (host arithmetic on the bit pattern)."""
+    b = np.asarray(p, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _norm(rng):
+    return np.concatenate([rng.normal(0, 0.5, OM.IN), np.exp(rng.normal(0, 0.3, OM.IN))]).astype(np.float32)
+
+
+def _net(seed, rng):
+    mlp = S.sme_mlp_create(seed)
+    p = S.sme_mlp_get_params(mlp)[0]
+    o = np.cumsum([0] + [size for _, size in OM.SIZES])
+    for b in (1, 3, 5):  # b1, b2, b3: zero after He initialisation, nonzero here so that every term is exercised
+        p[o[b]:o[b + 1]] = rng.normal(0, 0.3, o[b + 1] - o[b]).astype(np.float32)
+    S.sme_mlp_set_params(mlp, p, _norm(rng))
+    return mlp
+
+
+def test_bf16_helper_rounds_to_nearest_even():
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -2.5 + 2 ** -9, 1.0 + 2 ** -7], np.float32)
+    np.testing.assert_array_equal(_bf16(x), [1.0, 1.0, 1.0 + 2 ** -6, -2.5, 1.0 + 2 ** -7])
+
+
+@pytest.mark.parametrize("N", [1, 31, 1000, 40000])
+def test_forward_matches_oracle(N):
+    rng = np.random.default_rng(N)
+    mlp = _net(7, rng)
+    try:
+        p, nrm = S.sme_mlp_get_params(mlp)
+        X = rng.normal(0, 1.5, (N, OM.IN)).astype(np.float32)
+        y = torch.full((N,), np.nan, dtype=torch.float32, device="cuda")
+        S.sme_mlp_forward(mlp, torch.from_numpy(X).cuda(), y)
+        torch.cuda.synchronize()
+        ref, _ = OM.forward(_bf16(p), X, nrm.astype(np.float64))
+        got = y.cpu().double().numpy()
+        # FP32 accumulation over 128 products per unit: a few ulps of the magnitudes involved.
+        scale = 1.0 + np.abs(ref)
+        assert np.max(np.abs(got - ref) / scale) < 2e-5
+    finally:
+        S.sme_mlp_destroy(mlp)
+
+
+@pytest.mark.parametrize("N", [5, 32 * 152 * 2 + 17])
+def test_gradient_matches_oracle_and_is_deterministic(N):
+    rng = np.random.default_rng(100 + N)
+    mlp = _net(11, rng)
+    try:
+        p, nrm = S.sme_mlp_get_params(mlp)
+        X = rng.normal(0, 1.5, (N, OM.IN)).astype(np.float32)
+        tgt = rng.normal(0, 2.0, N).astype(np.float32)
+        Xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(tgt).cuda()
+        g1 = torch.zeros(OM.COUNT, dtype=torch.float32, device="cuda")
+        g2 = torch.zeros_like(g1)
+        loss = S.sme_mlp_gradient(mlp, Xd, td, g1)
+        S.sme_mlp_gradient(mlp, Xd, td, g2)
+        assert torch.equal(g1, g2)
+        ref_loss, ref_g = OM.loss_and_gradient(_bf16(p), X, tgt, nrm.astype(np.float64))
+        assert abs(loss - ref_loss) <= 1e-5 * ref_loss
+        g = g1.cpu().double().numpy()
+        assert np.linalg.norm(g - ref_g) <= 1e-4 * np.linalg.norm(ref_g)
+        # Each block of the layout separately, so that a wrong offset cannot hide in a larger block.
+        o = 0
+        for name, size in OM.SIZES:
+            blk = slice(o, o + size)
+            assert np.linalg.norm(g[blk] - ref_g[blk]) <= 1e-4 * np.linalg.norm(ref_g[blk]) + 1e-7, name
+            o += size
+    finally:
+        S.sme_mlp_destroy(mlp)
+
+
+def test_adam_first_step():
+    """First Adam step from zero moments: p - lr * g / (|g| + eps) (bias corrections cancel)."""
+    rng = np.random.default_rng(5)
+    mlp = _net(13, rng)
+    try:
+        p, nrm = S.sme_mlp_get_params(mlp)
+        N = 3000
+        X = rng.normal(0, 1, (N, OM.IN)).astype(np.float32)
+        tgt = rng.normal(0, 1, N).astype(np.float32)
+        _, g = OM.loss_and_gradient(_bf16(p), X, tgt, nrm.astype(np.float64))
+        lr = 1e-3
+        S.sme_mlp_train_step(mlp, torch.from_numpy(X).cuda(), torch.from_numpy(tgt).cuda(), lr)
+        p1 = S.sme_mlp_get_params(mlp)[0].astype(np.float64)
+        big = np.abs(g) > 1e-3 * np.abs(g).max()
+        np.testing.assert_allclose(p1[big], (p - lr * np.sign(g))[big], rtol=0, atol=2e-6)
+        assert np.all(np.abs(p1 - p) <= lr * 1.0001)
+    finally:
+        S.sme_mlp_destroy(mlp)
+
+
+def test_training_fits_a_smooth_function():
+    rng = np.random.default_rng(6)
+    mlp = S.sme_mlp_create(3)
+    try:
+        N = 50000
+        X = rng.normal(0, 1, (N, OM.IN)).astype(np.float32)
+        y = (np.sin(X[:, 0]) + 0.5 * X[:, 1] * X[:, 2] - 0.3 * X[:, 3]).astype(np.float32)
+        S.sme_mlp_set_params(mlp, None, np.concatenate([np.zeros(8), np.ones(8)]).astype(np.float32))
+        Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+        first = S.sme_mlp_gradient(mlp, Xd, yd)
+        for _ in range(300):
+            S.sme_mlp_train_step(mlp, Xd, yd, 3e-3)
+        last = S.sme_mlp_gradient(mlp, Xd, yd)
+        assert last < 0.05 * first, (first, last)
+    finally:
+        S.sme_mlp_destroy(mlp)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_features_match_oracle(dtype):
+    A = I.sparse_variable_row_nnz(700, 300, 0, 20, 4, var=2.0, dtype=dtype)
+    op = S.sme_op_create_csr(A.m, A.n, A.row_ptr, A.col_idx, A.vals)
+    try:
+        Fr = torch.zeros((A.m, 8), dtype=torch.float32, device="cuda")
+        Fc = torch.zeros((A.n, 8), dtype=torch.float32, device="cuda")
+        S.sme_op_features(op, 9, Fr, Fc)
+        Fr, Fc = Fr.cpu().double().numpy(), Fc.cpu().double().numpy()
+    finally:
+        S.sme_op_destroy(op)
+    z_r = O.row_estimate(A, np.zeros(A.m), np.zeros(A.n), O.probe_signs(9, 1, 0, A.n, 8))
+    z_c = O.col_estimate(A, np.zeros(A.m), np.zeros(A.n), O.probe_signs(9, 1, 1, A.m, 8))
+    rows = np.repeat(np.arange(A.m), np.diff(A.row_ptr))
+    vals = np.asarray(A.vals, np.float64)
+    nnz_r = np.bincount(rows[vals != 0], minlength=A.m)
+    nnz_c = np.bincount(A.col_idx[vals != 0], minlength=A.n)
+    sabs_r = np.bincount(rows, np.abs(vals), minlength=A.m)
+    sabs_c = np.bincount(A.col_idx, np.abs(vals), minlength=A.n)
+    f0 = lambda z: 0.5 * np.log(np.maximum(z, 1e-30))
+    mean_abs = lambda s, c: np.log(np.maximum(np.where(c > 0, s / np.maximum(c, 1), 0.0), 1e-30))
+    tol = 1e-4 if dtype == np.float32 else 1e-5
+    for F, z, c, s, side in ((Fr, z_r, nnz_r, sabs_r, 0.0), (Fc, z_c, nnz_c, sabs_c, 1.0)):
+        nz = z > 0
+        np.testing.assert_allclose(F[nz, 0], f0(z[nz]), atol=tol)
+        np.testing.assert_allclose(F[:, 1], np.log1p(c), atol=1e-6)
+        np.testing.assert_allclose(F[c > 0, 2], mean_abs(s, c)[c > 0], atol=1e-5)
+        assert np.all(F[:, 3] == side)
+        np.testing.assert_allclose(F[:, 4], f0(z_r).mean(), atol=1e-4)
+        np.testing.assert_allclose(F[:, 5], f0(z_c).mean(), atol=1e-4)
+        np.testing.assert_allclose(F[:, 6], np.log(A.m), rtol=1e-6)
+        np.testing.assert_allclose(F[:, 7], np.log(A.n), rtol=1e-6)
+    assert (nnz_r == 0).any()  # the generator's empty rows are covered
+
+
+def test_warm_start_beats_zero_start_on_held_out_matrices():
+    """Train on one family sample, then on unseen matrices of the same family: after the same short run, the
+    warm-started average has a lower objective (eq. (3)) than Algorithm 1 from zero."""
+    from paper_1602_06621_gb300 import warmstart as W
+    mats = I.batched_family(14, 800, 6000, seed=21)
+    train, held = mats[:10], mats[10:]
+    X, y = W.training_set(train, T=400, k=32, seed=1)
+    mlp = S.sme_mlp_create(0)
+    try:
+        hist = W.train(mlp, X, y, steps=800, batch=8192, lr=2e-3)
+        assert hist[-1][1] < 0.5 * hist[0][1], hist
+        for i, A in enumerate(held):
+            _, _, zero = W.run(A, T=20, k=32, seed=50 + i)
+            _, _, warm = W.run(A, T=20, k=32, seed=50 + i, mlp=mlp, t0=W.WARM_T0)
+            _, _, long = W.run(A, T=400, k=32, seed=50 + i)
+            assert warm["objective"] < zero["objective"], (i, zero, warm)
+            # 20 warm-started iterations come close to 400 from zero (RMS within a factor 2; zero-started
+            # runs of 20 iterations are still several times worse).
+            assert warm["rms"] < 0.3 * zero["rms"], (i, zero, warm)
+            assert warm["rms"] < 2.0 * long["rms"], (i, long, warm)
+    finally:
+        S.sme_mlp_destroy(mlp)
