@@ -32,7 +32,8 @@ if ROOT not in sys.path:
 METRIC = "equilibration probe-pairs/s + HBM GB/s; time to LSQR 1e-6 vs plain, 1×GB300"
 UNIT = "probe-pairs/s"
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCE = os.path.join(ROOT, "paper_1602_06621_gb300", "csrc", "equilibrate.cu")
+# The iteration kernel's sources: recorded ncu traffic is used only while these are unchanged.
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1602_06621_gb300", "csrc", f) for f in ("equilibrate.cu", "sme_internal.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sgd_iteration_f32_k32_large.txt")
 
 
@@ -85,7 +86,10 @@ def measured_hbm_peak():
 def recorded_traffic():
     """ncu DRAM bytes per launch of the iteration kernel, if taken on the current kernel source."""
     try:
-        src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+        h = hashlib.sha256()
+        for f in KERNEL_SOURCES:
+            h.update(open(f, "rb").read())
+        src = h.hexdigest()
         vals = {}
         for line in open(TRAFFIC_FILE):
             if "=" in line and not line.lstrip().startswith("#"):
