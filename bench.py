@@ -49,9 +49,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lsqr", action="store_true")
-    ap.add_argument("--workload", choices=["large", "dense", "batched"], default="large",
+    ap.add_argument("--workload", choices=["large", "dense", "batched", "learned"], default="large",
                     help="large: the sparse 1e6 x 5e5 step (default); dense: 16384^2 BF16 tensor-core step; "
-                         "batched: 512 matrices of uneven size in one operator")
+                         "batched: 512 matrices of uneven size in one operator; learned: warm start vs zero "
+                         "start to a norm spread of 1.05 on 500 held-out matrices")
     return ap.parse_args()
 
 
@@ -342,6 +343,166 @@ def run_batched(args, rank, world, local):
 
 # ------------------------------------------------------------------------------------------ our arm
 
+def run_learned(args, rank, world, local):
+    """The learned warm start on the batched family (m log-uniform in [1e3, 2e4 * scale]).
+
+    Training: 300 matrices labelled with the scalings Algorithm 1 converges to (gamma = 0.1, T = 400,
+    k = 32, one batched run), features from the library's feature kernel, the MLP trained by the library's
+    own kernels.  Evaluation: 500 held-out matrices in one batch, at gamma = 1e-3 (where the regularised
+    optimum allows a row/column norm spread of 1.05), three ways: the paper's method (zero start, t0 = 0);
+    zero start with the warm start's step offset; the network's prediction with that offset.  Per matrix,
+    the first multiple of 100 iterations whose average reaches spread <= 1.05 (up to 3000); then each arm is
+    timed (features and network included) for the iterations that bring every matrix there, or for 3000
+    when some never get there, followed by per-matrix LSQR to 1e-6; plain LSQR is timed beside them."""
+    import numpy as np
+    import scipy.sparse as sps
+    import torch
+
+    from paper_1602_06621_gb300 import inputs as I
+    from paper_1602_06621_gb300 import sme
+    from paper_1602_06621_gb300 import warmstart as W
+
+    m_hi = max(2000, int(2e4 * args.scale))
+    n_train, n_eval = 300, 500
+    workers = min(16, os.cpu_count() or 1)
+    g0 = time.perf_counter()
+    train = I.batched_family(n_train, 1000, m_hi, seed=60 + rank, workers=workers)
+    held = I.batched_family(n_eval, 1000, m_hi, seed=70 + rank, workers=workers)
+    gen_s = time.perf_counter() - g0
+    torch.cuda.set_device(local)
+    f32 = dict(dtype=torch.float32, device="cuda")
+    k, gamma, target, T_max, chunk, t0 = 32, W.SPREAD_GAMMA, 1.05, 3000, 100, W.SPREAD_T0
+
+    # Training (outside the timed region).
+    tr0 = time.perf_counter()
+    bt = sme.sme_batch_create(train)
+    train_rows = sum(A.m + A.n for A in train)
+    del train
+    X, y = W.batch_training_set(bt, T=400, k=32, seed=1)
+    torch.cuda.synchronize()
+    label_s = time.perf_counter() - tr0
+    sme.sme_batch_destroy(bt)
+    mlp = sme.sme_mlp_create(0)
+    tr1 = time.perf_counter()
+    hist = W.train(mlp, X, y, steps=1500, batch=16384, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - tr1
+    del X, y
+
+    # Held-out batch and right-hand sides b = A x* per matrix.
+    b = sme.sme_batch_create(held)
+    _, ro, co = sme.sme_batch_get_info(b)
+    M, N = int(ro[-1]), int(co[-1])
+    nnz = sum(A.nnz for A in held)
+    xs, bs = [], []
+    for i, A in enumerate(held):
+        x_i = I.normal_vector(A.n, 500 + i, np.float64)
+        bs.append(sps.csr_matrix((A.vals.astype(np.float64), A.col_idx, A.row_ptr), shape=(A.m, A.n)) @ x_i)
+    bvec = torch.tensor(np.concatenate(bs).astype(np.float32), device="cuda")
+    del held, bs
+
+    arms = {"zero (paper's method)": ("zero", 0), f"zero start, t0={t0}": ("zero", t0),
+            f"warm start, t0={t0}": ("warm", t0)}
+
+    def start(kind):
+        u, v = torch.zeros(M, **f32), torch.zeros(N, **f32)
+        if kind == "warm":
+            sme.sme_batch_warm_start(b, mlp, 3, u, v)
+        return u, v, u.clone(), v.clone()
+
+    def spreads(ub, vb):
+        ev = sme.sme_batch_evaluate(b, ub, vb, gamma=gamma)
+        return np.array([max(e["row_spread"], e["col_spread"]) for e in ev])
+
+    out = {}
+    for name, (kind, off) in arms.items():
+        u, v, ub, vb = start(kind)
+        first = np.full(n_eval, -1)
+        sp0 = spreads(ub, vb)
+        for c in range(T_max // chunk):
+            sme.sme_batch_equilibrate(b, u, v, ub, vb, T=chunk, k=k, t_begin=1 + c * chunk, t0=off, seed=0,
+                                      gamma=gamma, flags=sme.SME_EQ_NO_GRAPH)
+            sp = spreads(ub, vb)
+            first[(first < 0) & (sp <= target)] = (c + 1) * chunk
+        reached = first > 0
+        T_arm = int(first.max()) if reached.all() else T_max
+
+        def run_arm():
+            u, v, ub, vb = start(kind)
+            sme.sme_batch_equilibrate(b, u, v, ub, vb, T=T_arm, k=k, t0=off, seed=0, gamma=gamma,
+                                      flags=sme.SME_EQ_ASYNC)
+            return ub, vb
+
+        for _ in range(args.warmup):
+            run_arm()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                ub, vb = run_arm()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        sme.sme_op_check(sme.sme_batch_op(b))
+        eq_ms = e0.elapsed_time(e1) / args.steps
+        final = spreads(ub, vb)
+        x = torch.zeros(N, **f32)
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        lr = sme.sme_batch_lsqr(b, ub, vb, bvec, x, tol=1e-6, max_iters=20000, check_every=10)
+        l1.record(stream)
+        l1.synchronize()
+        its = np.array([r["iters"] for r in lr])
+        out[name] = {
+            "iterations_to_spread": {"reached": int(reached.sum()), "of": n_eval,
+                                     "median": float(np.median(first[reached])) if reached.any() else None,
+                                     "p90": float(np.percentile(first[reached], 90)) if reached.any() else None,
+                                     "max": int(first.max()) if reached.any() else None,
+                                     "spread_at_start_median": float(np.median(sp0)),
+                                     "spread_at_3000_median": float(np.median(sp)),
+                                     "spread_at_3000_max": float(sp.max())},
+            "timed_T": T_arm, "equilibrate_ms": eq_ms, "all_reached": bool(reached.all()),
+            "final_spread_median": float(np.median(final)), "final_spread_max": float(final.max()),
+            "lsqr": {"ms": l0.elapsed_time(l1), "iters_median": float(np.median(its)), "iters_max": int(its.max()),
+                     "converged": int(sum(r["converged"] for r in lr))},
+            "time_to_lsqr_1e-6_ms": eq_ms + l0.elapsed_time(l1), "clocks": clk.summary(),
+        }
+    xp = torch.zeros(N, **f32)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(torch.cuda.current_stream())
+    pl = sme.sme_batch_lsqr(b, None, None, bvec, xp, tol=1e-6, max_iters=20000, check_every=100)
+    p1.record(torch.cuda.current_stream())
+    p1.synchronize()
+    pits = np.array([r["iters"] for r in pl])
+    warm = out[f"warm start, t0={t0}"]
+    if rank == 0:
+        line = {
+            "metric": "learned warm start: wall-time to row/column norm spread <= 1.05 (gamma 1e-3), "
+                      "500 held-out matrices in one batch",
+            "value": warm["equilibrate_ms"] if warm["all_reached"] else None, "unit": "ms",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"learned warm start: batched family, m log-uniform in [1e3, {m_hi}], "
+                                   f"n = m U[0.3,1], 5-50 nonzeros per row, FP32, factors of variance 2; "
+                                   f"{n_train} training matrices, {n_eval} held-out; k={k}, gamma={gamma}, "
+                                   f"target spread {target}",
+                       "rows": M, "cols": N, "nnz": nnz, "k": k, "gamma": gamma,
+                       "l2": f"inputs larger than L2 ({16 * nnz / 1e6:.0f} MB per iteration)"},
+            "training": {"matrices": n_train, "samples": train_rows, "label_T": 400, "label_gamma": 0.1,
+                         "steps": 1500, "batch": 16384, "loss_first": hist[0][1], "loss_last": hist[-1][1],
+                         "label_s": label_s, "train_s": train_s, "generate_s": gen_s},
+            "arms": out,
+            "plain_lsqr": {"ms": p0.elapsed_time(p1), "iters_median": float(np.median(pits)),
+                           "iters_max": int(pits.max()), "converged": int(sum(r["converged"] for r in pl)),
+                           "iteration_cap": 20000},
+        }
+        print(json.dumps(line), flush=True)
+    sme.sme_mlp_destroy(mlp)
+    sme.sme_batch_destroy(b)
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -353,6 +514,8 @@ def main():
         return run_dense(args, rank, world, local)
     if args.workload == "batched":
         return run_batched(args, rank, world, local)
+    if args.workload == "learned":
+        return run_learned(args, rank, world, local)
 
     import numpy as np
     import torch

@@ -309,6 +309,16 @@ sme_status sme_batch_lsqr(sme_batch b, const void *u_bar, const void *v_bar, con
  * of all matrices at once (row / column norms come back concatenated). */
 sme_status sme_batch_op(sme_batch b, sme_op *op);
 
+/*
+ * sme_batch_evaluate -- sme_evaluate for every matrix of the batch: res is a HOST array of one
+ * sme_eval_result per matrix (spread over that matrix's nonempty rows / columns, RMS against its own
+ * targets, its own f(u, v) of eq. (3)).  alpha, beta <= 0 select each matrix's Section 4 defaults
+ * (n_b/m_b)^(1/4), (m_b/n_b)^(1/4); gamma <= 0 selects 0.1.  u, v: concatenated state vectors.
+ * Synchronises `stream`.
+ */
+sme_status sme_batch_evaluate(sme_batch b, const void *u, const void *v, double alpha, double beta, double gamma,
+                              sme_eval_result *res, void *stream);
+
 /* ------------------------------------------------------------------ learned warm start */
 
 /*
@@ -342,10 +352,14 @@ sme_status sme_mlp_gradient(sme_mlp mlp, const float *X, const float *target, in
 /* One Adam step (beta1 0.9, beta2 0.999) on the same loss with learning rate lr. */
 sme_status sme_mlp_train_step(sme_mlp mlp, const float *X, const float *target, int64_t N, float lr, float *loss,
                               void *stream);
-/* Features of every row (m x 8) and column (n x 8) of a sparse operator, device float arrays. */
+/* Features of every row (m x 8) and column (n x 8) of a sparse operator, device float arrays.  For the
+ * operator of a batch, the mean sketch norms and the sizes are those of each row's / column's own matrix. */
 sme_status sme_op_features(sme_op op, uint64_t seed, float *row_features, float *col_features, void *stream);
 /* u0[m], v0[n] (state type) = the MLP's prediction for every row and column of `op`. */
 sme_status sme_warm_start(sme_op op, sme_mlp mlp, uint64_t seed, void *u0, void *v0, void *stream);
+/* The same two for all matrices of a batch (concatenated rows, concatenated columns). */
+sme_status sme_batch_features(sme_batch b, uint64_t seed, float *row_features, float *col_features, void *stream);
+sme_status sme_batch_warm_start(sme_batch b, sme_mlp mlp, uint64_t seed, void *u0, void *v0, void *stream);
 
 /* ------------------------------------------------------------------ allocation-free estimator */
 

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "sme_internal.cuh"
@@ -160,6 +161,107 @@ static sme_status evaluate_t(sme_op op, const real *u, const real *v, double alp
                      0.5 * gamma * (R.sum_x2 + C.sum_x2);
     res->empty_rows = (int64_t)R.empty;
     res->empty_cols = (int64_t)C.empty;
+    return SME_OK;
+}
+
+// Per-matrix partials of a batch: block (b, side) reduces matrix b's rows (side 0) or columns (side 1), whose
+// entries are off[b] .. off[b+1]-1 in the batch's original order; targets[side][b] is the matrix's norm target.
+template <typename real>
+__global__ void __launch_bounds__(EV_THREADS) segment_eval(int count, const int64_t *off_r, const int64_t *off_c,
+                                                           const double *r2, const double *c2, const real *u,
+                                                           const real *v, const double *targets, EvalPart *parts)
+{
+    __shared__ EvalPart sh[EV_THREADS];
+    const int b = blockIdx.x, side = blockIdx.y;
+    const int64_t *off = side ? off_c : off_r;
+    const double *q = side ? c2 : r2;
+    const real *x = side ? v : u;
+    const double target = targets[side * count + b];
+    EvalPart p{0, 0, 0, 0, 0, INFINITY, 0};
+    for (int64_t i = off[b] + threadIdx.x; i < off[b + 1]; i += blockDim.x) {
+        const double w = q[i];
+        const double nv = sqrt(w);
+        p.sum_sq_dev += (nv - target) * (nv - target);
+        p.sum_r2 += w;
+        const double xi = (double)x[i];
+        p.sum_x += xi;
+        p.sum_x2 += xi * xi;
+        if (w > 0) {
+            p.maxn = fmax(p.maxn, nv);
+            p.minn = fmin(p.minn, nv);
+        } else {
+            p.empty += 1.0;
+        }
+    }
+    sh[threadIdx.x] = p;
+    __syncthreads();
+    for (int o = EV_THREADS / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            EvalPart &a = sh[threadIdx.x];
+            const EvalPart &c = sh[threadIdx.x + o];
+            a.sum_sq_dev += c.sum_sq_dev;
+            a.sum_r2 += c.sum_r2;
+            a.sum_x += c.sum_x;
+            a.sum_x2 += c.sum_x2;
+            a.maxn = fmax(a.maxn, c.maxn);
+            a.minn = fmin(a.minn, c.minn);
+            a.empty += c.empty;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) parts[side * count + b] = sh[0];
+}
+
+template <typename real>
+static sme_status batch_evaluate_t(sme_op op, const real *u, const real *v, double alpha, double beta, double gamma,
+                                   sme_eval_result *res, cudaStream_t s)
+{
+    const BatchInfo *B = op->batch;
+    const int count = B->count;
+    const int64_t m = op->m, n = op->n;
+    std::vector<int64_t> offs(2 * (count + 1));
+    std::memcpy(offs.data(), B->row_off, (count + 1) * sizeof(int64_t));
+    std::memcpy(offs.data() + count + 1, B->col_off, (count + 1) * sizeof(int64_t));
+    std::vector<double> al(count), be(count), targets(2 * count);
+    for (int b = 0; b < count; ++b) {
+        const double mb = (double)(B->row_off[b + 1] - B->row_off[b]), nb = (double)(B->col_off[b + 1] - B->col_off[b]);
+        al[b] = alpha > 0 ? alpha : std::pow(nb / mb, 0.25);
+        be[b] = beta > 0 ? beta : std::pow(mb / nb, 0.25);
+        targets[b] = al[b];
+        targets[count + b] = be[b];
+    }
+    char *buf = nullptr;
+    const size_t bytes = (size_t)(2 * (m + n)) * 8 + offs.size() * 8 + targets.size() * 8 + 2 * count * sizeof(EvalPart);
+    SME_CUDA(cudaMallocAsync((void **)&buf, bytes, s));
+    double *sq_u = (double *)buf, *sq_v = sq_u + m, *r2 = sq_v + n, *c2 = r2 + m;
+    int64_t *d_off = (int64_t *)(c2 + n);
+    double *d_tg = (double *)(d_off + offs.size());
+    EvalPart *parts = (EvalPart *)(d_tg + targets.size());
+    SME_CUDA(cudaMemcpyAsync(d_off, offs.data(), offs.size() * 8, cudaMemcpyHostToDevice, s));
+    SME_CUDA(cudaMemcpyAsync(d_tg, targets.data(), targets.size() * 8, cudaMemcpyHostToDevice, s));
+    exp2_sorted<real><<<nblk(m), 256, 0, s>>>(m, op->fwd.perm, u, sq_u);
+    exp2_sorted<real><<<nblk(n), 256, 0, s>>>(n, op->bwd.perm, v, sq_v);
+    exact_norms_kernel<real><<<nblk(op->fwd.nslices * 32), 256, 0, s>>>(op->fwd, op->dbl, sq_v, u, r2);
+    exact_norms_kernel<real><<<nblk(op->bwd.nslices * 32), 256, 0, s>>>(op->bwd, op->dbl, sq_u, v, c2);
+    segment_eval<real><<<dim3(count, 2), EV_THREADS, 0, s>>>(count, d_off, d_off + count + 1, r2, c2, u, v, d_tg,
+                                                             parts);
+    SME_CUDA(cudaGetLastError());
+    std::vector<EvalPart> h(2 * count);
+    SME_CUDA(cudaMemcpyAsync(h.data(), parts, h.size() * sizeof(EvalPart), cudaMemcpyDeviceToHost, s));
+    SME_CUDA(cudaStreamSynchronize(s));
+    SME_CUDA(cudaFreeAsync(buf, s));
+    for (int b = 0; b < count; ++b) {
+        const EvalPart &R = h[b], &C = h[count + b];
+        sme_eval_result &o = res[b];
+        o.row_spread = R.minn > 0 && std::isfinite(R.minn) ? R.maxn / R.minn : INFINITY;
+        o.col_spread = C.minn > 0 && std::isfinite(C.minn) ? C.maxn / C.minn : INFINITY;
+        const double len = (double)(offs[b + 1] - offs[b] + offs[count + 2 + b] - offs[count + 1 + b]);
+        o.rms = std::sqrt(R.sum_sq_dev + C.sum_sq_dev) / std::sqrt(len);
+        o.objective = 0.5 * R.sum_r2 - al[b] * al[b] * R.sum_x - be[b] * be[b] * C.sum_x +
+                      0.5 * gamma * (R.sum_x2 + C.sum_x2);
+        o.empty_rows = (int64_t)R.empty;
+        o.empty_cols = (int64_t)C.empty;
+    }
     return SME_OK;
 }
 
@@ -622,6 +724,22 @@ extern "C" sme_status sme_evaluate(sme_op op, const void *u, const void *v, doub
                                   (cudaStream_t)stream);
     return evaluate_t<float>(op, (const float *)u, (const float *)v, alpha, beta, gamma, r2, c2, res,
                              (cudaStream_t)stream);
+}
+
+extern "C" sme_status sme_batch_evaluate(sme_batch bt, const void *u, const void *v, double alpha, double beta,
+                                         double gamma, sme_eval_result *res, void *stream)
+{
+    if (!bt || !u || !v || !res) {
+        set_error("sme_batch_evaluate: bad arguments");
+        return SME_ERR_ARG;
+    }
+    if (gamma <= 0) gamma = 0.1;
+    sme_op op = bt->op;
+    if (op->dbl)
+        return batch_evaluate_t<double>(op, (const double *)u, (const double *)v, alpha, beta, gamma, res,
+                                        (cudaStream_t)stream);
+    return batch_evaluate_t<float>(op, (const float *)u, (const float *)v, alpha, beta, gamma, res,
+                                   (cudaStream_t)stream);
 }
 
 extern "C" sme_status sme_lsqr(sme_op op, const void *u_bar, const void *v_bar, const void *b, void *x,

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "sme_internal.cuh"
@@ -295,38 +296,55 @@ __global__ void side_stats(Sell S, float *cnt, float *meanabs)
     meanabs[i] = c ? (float)(sabs / c) : 0.f;
 }
 
-// Feature rows: [log sketch norm, log(1 + nnz), log mean|a|, side, mean sketch of rows, of columns, log m, log n].
+// Matrix of entry i when the entries of matrix b are off[b] .. off[b+1]-1 (count matrices).
+__device__ __forceinline__ int segment_of(const int64_t *off, int count, int64_t i)
+{
+    int lo = 0, hi = count;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Feature rows: [log sketch norm, log(1 + nnz), log mean|a|, side, mean sketch of the matrix's rows, of its
+// columns, log m, log n], each matrix of a batch with its own means and sizes.
 template <typename real>
 __global__ void assemble_features(int64_t len, const real *z, const float *cnt, const float *meanabs, float side,
-                                  float mu_r, float mu_c, float lm, float ln, float *F)
+                                  int count, const int64_t *off_own, const int64_t *off_r, const int64_t *off_c,
+                                  const float *mu_r, const float *mu_c, float *F)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= len) return;
+    const int b = segment_of(off_own, count, i);
     float *f = F + i * MLP_IN;
     f[0] = 0.5f * logf(fmaxf((float)z[i], 1e-30f));
     f[1] = log1pf(cnt[i]);
     f[2] = logf(fmaxf(meanabs[i], 1e-30f));
     f[3] = side;
-    f[4] = mu_r;
-    f[5] = mu_c;
-    f[6] = lm;
-    f[7] = ln;
+    f[4] = mu_r[b];
+    f[5] = mu_c[b];
+    f[6] = logf((float)(off_r[b + 1] - off_r[b]));
+    f[7] = logf((float)(off_c[b + 1] - off_c[b]));
 }
 
+// Mean of 1/2 log(sketch) over each matrix's entries (FP64 sums): one CTA per matrix.
 template <typename real>
-__global__ void sum_log_sketch(int64_t len, const real *z, double *out)
+__global__ void __launch_bounds__(1024) segment_mean_log_sketch(const int64_t *off, const real *z, float *out)
 {
-    __shared__ double sh[256];
+    __shared__ double sh[1024];
+    const int b = blockIdx.x;
+    const int64_t lo = off[b], hi = off[b + 1];
     double v = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
-        v += 0.5 * log(fmax((double)z[i], 1e-30));
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v += 0.5 * log(fmax((double)z[i], 1e-30));
     sh[threadIdx.x] = v;
     __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
+    for (int o = 512; o > 0; o >>= 1) {
         if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+    if (threadIdx.x == 0) out[b] = (float)(sh[0] / (double)(hi - lo));
 }
 
 template <typename real>
@@ -345,29 +363,36 @@ template <typename real>
 static sme_status features_t(sme_op op, uint64_t seed, float *rowF, float *colF, cudaStream_t s)
 {
     const int64_t m = op->m, n = op->n;
+    // Matrix boundaries: one matrix for a single operator, the batch's offsets otherwise.
+    const int count = op->batch ? op->batch->count : 1;
+    std::vector<int64_t> offs(2 * (count + 1));
+    if (op->batch) {
+        std::memcpy(offs.data(), op->batch->row_off, (count + 1) * sizeof(int64_t));
+        std::memcpy(offs.data() + count + 1, op->batch->col_off, (count + 1) * sizeof(int64_t));
+    } else {
+        offs = {0, m, 0, n};
+    }
     char *buf = nullptr;
-    const size_t bytes = (size_t)(m + n) * (sizeof(real) * 2 + 8) + 2 * 152 * sizeof(double);
+    const size_t bytes = (size_t)(m + n) * (sizeof(real) * 2 + 8) + offs.size() * 8 + 2 * (size_t)count * 4 + 64;
     SME_CUDA(cudaMallocAsync((void **)&buf, bytes, s));
     real *u0 = (real *)buf, *v0 = u0 + m, *zu = v0 + n, *zv = zu + m;
     float *cnt = (float *)(zv + n), *mab = cnt + (m + n);
-    double *part = (double *)(mab + (m + n));
+    int64_t *d_off = (int64_t *)(((uintptr_t)(mab + (m + n)) + 15) & ~(uintptr_t)15);
+    float *mu = (float *)(d_off + offs.size());
+    SME_CUDA(cudaMemcpyAsync(d_off, offs.data(), offs.size() * 8, cudaMemcpyHostToDevice, s));
     SME_CUDA(cudaMemsetAsync(u0, 0, (size_t)(m + n) * sizeof(real), s));
     SME_TRY(estimate_sparse(op, u0, v0, 1, 8, seed, 0, zu, zv, s));
     side_stats<real><<<nblk(m), 256, 0, s>>>(op->fwd, cnt, mab);
     side_stats<real><<<nblk(n), 256, 0, s>>>(op->bwd, cnt + m, mab + m);
-    sum_log_sketch<real><<<152, 256, 0, s>>>(m, zu, part);
-    sum_log_sketch<real><<<152, 256, 0, s>>>(n, zv, part + 152);
-    std::vector<double> h(2 * 152);
-    SME_CUDA(cudaMemcpyAsync(h.data(), part, h.size() * 8, cudaMemcpyDeviceToHost, s));
-    SME_CUDA(cudaStreamSynchronize(s));
-    double sr = 0, sc = 0;
-    for (int b = 0; b < 152; ++b) {
-        sr += h[b];
-        sc += h[152 + b];
-    }
-    const float mu_r = (float)(sr / m), mu_c = (float)(sc / n), lm = logf((float)m), ln = logf((float)n);
-    if (rowF) assemble_features<real><<<nblk(m), 256, 0, s>>>(m, zu, cnt, mab, 0.f, mu_r, mu_c, lm, ln, rowF);
-    if (colF) assemble_features<real><<<nblk(n), 256, 0, s>>>(n, zv, cnt + m, mab + m, 1.f, mu_r, mu_c, lm, ln, colF);
+    const int64_t *off_r = d_off, *off_c = d_off + count + 1;
+    segment_mean_log_sketch<real><<<count, 1024, 0, s>>>(off_r, zu, mu);
+    segment_mean_log_sketch<real><<<count, 1024, 0, s>>>(off_c, zv, mu + count);
+    if (rowF)
+        assemble_features<real><<<nblk(m), 256, 0, s>>>(m, zu, cnt, mab, 0.f, count, off_r, off_r, off_c, mu,
+                                                        mu + count, rowF);
+    if (colF)
+        assemble_features<real><<<nblk(n), 256, 0, s>>>(n, zv, cnt + m, mab + m, 1.f, count, off_c, off_r, off_c, mu,
+                                                        mu + count, colF);
     SME_CUDA(cudaGetLastError());
     SME_CUDA(cudaFreeAsync(buf, s));
     return SME_OK;
@@ -529,8 +554,8 @@ extern "C" sme_status sme_mlp_train_step(sme_mlp M, const float *X, const float 
 extern "C" sme_status sme_op_features(sme_op op, uint64_t seed, float *row_features, float *col_features,
                                       void *stream)
 {
-    if (!op || op->dense || op->batch) {
-        set_error("sme_op_features: sparse single operators only");
+    if (!op || op->dense) {
+        set_error("sme_op_features: sparse operators only");
         return SME_ERR_ARG;
     }
     if (op->dbl) return features_t<double>(op, seed, row_features, col_features, (cudaStream_t)stream);
@@ -539,7 +564,7 @@ extern "C" sme_status sme_op_features(sme_op op, uint64_t seed, float *row_featu
 
 extern "C" sme_status sme_warm_start(sme_op op, sme_mlp M, uint64_t seed, void *u0, void *v0, void *stream)
 {
-    if (!op || !M || !u0 || !v0 || op->dense || op->batch) {
+    if (!op || !M || !u0 || !v0 || op->dense) {
         set_error("sme_warm_start: bad arguments");
         return SME_ERR_ARG;
     }
@@ -560,4 +585,17 @@ extern "C" sme_status sme_warm_start(sme_op op, sme_mlp M, uint64_t seed, void *
     SME_CUDA(cudaGetLastError());
     SME_CUDA(cudaFreeAsync(buf, s));
     return SME_OK;
+}
+
+extern "C" sme_status sme_batch_features(sme_batch b, uint64_t seed, float *row_features, float *col_features,
+                                         void *stream)
+{
+    if (!b) return SME_ERR_ARG;
+    return sme_op_features(b->op, seed, row_features, col_features, stream);
+}
+
+extern "C" sme_status sme_batch_warm_start(sme_batch b, sme_mlp M, uint64_t seed, void *u0, void *v0, void *stream)
+{
+    if (!b) return SME_ERR_ARG;
+    return sme_warm_start(b->op, M, seed, u0, v0, stream);
 }

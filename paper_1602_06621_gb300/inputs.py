@@ -169,13 +169,23 @@ def workload_large(scale: float = 1.0, seed: int = 2) -> CSR:
     return sparse_fixed_row_nnz(m, n, 20, seed, var=2.0, dtype=np.float32)
 
 
+def _family_member(job):
+    m, n, lo, hi, s, var, dtype = job
+    return sparse_variable_row_nnz(m, n, lo, hi, s, var=var, dtype=dtype)
+
+
 def batched_family(count: int, m_lo: int, m_hi: int, seed: int, *, nnz_lo: int = 5, nnz_hi: int = 50,
-                   var: float = 2.0, dtype=np.float32):
+                   var: float = 2.0, dtype=np.float32, workers: int = 0):
     """count matrices: m log-uniform in [m_lo, m_hi], n = round(m * U[0.3, 1.0]), row lengths uniform
-    integers in [nnz_lo, nnz_hi] (capped at n), factors of variance `var`."""
+    integers in [nnz_lo, nnz_hi] (capped at n), factors of variance `var`.  workers > 1 generates the
+    matrices in that many spawned processes (same result; call it before the process touches the GPU)."""
     rng = np.random.default_rng(seed)
     ms = np.exp(rng.uniform(np.log(m_lo), np.log(m_hi), size=count)).round().astype(np.int64)
     ns = np.maximum(1, np.round(ms * rng.uniform(0.3, 1.0, size=count))).astype(np.int64)
     seeds = rng.integers(0, 2 ** 31, size=count)
-    return [sparse_variable_row_nnz(int(m), int(n), nnz_lo, nnz_hi, int(s), var=var, dtype=dtype)
-            for m, n, s in zip(ms, ns, seeds)]
+    jobs = [(int(m), int(n), nnz_lo, nnz_hi, int(s), var, dtype) for m, n, s in zip(ms, ns, seeds)]
+    if workers > 1 and count > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(workers, count)) as pool:
+            return pool.map(_family_member, jobs, chunksize=max(1, count // (4 * workers)))
+    return [_family_member(j) for j in jobs]

@@ -22,7 +22,8 @@ __all__ = [
     "sme_batch_get_info", "sme_batch_equilibrate", "sme_batch_estimate", "sme_batch_op", "sme_op_autotune", "sme_batch_lsqr",
     "sme_equilibrate_targets", "sme_equilibrate_symmetric", "sme_equilibrate_block", "sme_mlp_create",
     "sme_mlp_destroy", "sme_mlp_param_count", "sme_mlp_get_params", "sme_mlp_set_params", "sme_mlp_forward",
-    "sme_mlp_gradient", "sme_mlp_train_step", "sme_op_features", "sme_warm_start",
+    "sme_mlp_gradient", "sme_mlp_train_step", "sme_op_features", "sme_warm_start", "sme_batch_evaluate",
+    "sme_batch_features", "sme_batch_warm_start",
 ]
 SME_STATIC_MAX_COLS = 1 << 20
 
@@ -110,6 +111,9 @@ SIGNATURES = {
     "sme_mlp_train_step": ([_vp, _vp, _vp, _i64, ctypes.c_float, _vp, _vp], _i32),
     "sme_op_features": ([_vp, _u64, _vp, _vp, _vp], _i32),
     "sme_warm_start": ([_vp, _vp, _u64, _vp, _vp, _vp], _i32),
+    "sme_batch_evaluate": ([_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp, _vp], _i32),
+    "sme_batch_features": ([_vp, _u64, _vp, _vp, _vp], _i32),
+    "sme_batch_warm_start": ([_vp, _vp, _u64, _vp, _vp, _vp], _i32),
 }
 
 
@@ -411,3 +415,22 @@ def sme_op_features(op, seed, row_features, col_features, stream=None):
 
 def sme_warm_start(op, mlp, seed, u0, v0, stream=None):
     _check(load().sme_warm_start(op, mlp, int(seed), _ptr(u0), _ptr(v0), _stream(stream)), "sme_warm_start")
+
+
+def sme_batch_evaluate(b, u, v, alpha=0.0, beta=0.0, gamma=0.0, stream=None):
+    """Per-matrix evaluation of a batch; returns a list of dicts like sme_evaluate's."""
+    count = sme_batch_get_info(b)[0]
+    res = (sme_eval_result * count)()
+    _check(load().sme_batch_evaluate(b, _ptr(u), _ptr(v), float(alpha), float(beta), float(gamma),
+                                     ctypes.cast(res, ctypes.c_void_p), _stream(stream)), "sme_batch_evaluate")
+    return [{f: getattr(r, f) for f, _ in sme_eval_result._fields_} for r in res]
+
+
+def sme_batch_features(b, seed, row_features, col_features, stream=None):
+    _check(load().sme_batch_features(b, int(seed), _ptr(row_features), _ptr(col_features), _stream(stream)),
+           "sme_batch_features")
+
+
+def sme_batch_warm_start(b, mlp, seed, u0, v0, stream=None):
+    _check(load().sme_batch_warm_start(b, mlp, int(seed), _ptr(u0), _ptr(v0), _stream(stream)),
+           "sme_batch_warm_start")

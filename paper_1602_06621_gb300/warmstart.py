@@ -17,8 +17,14 @@ import numpy as np
 from . import sme
 
 FEATURES = 8
-# Step offset used after a warm start: the first step is then 2 / (gamma (WARM_T0 + 2)) instead of 1/gamma.
+# Step offset used after a warm start at the default gamma = 0.1: the first step is then
+# 2 / (gamma (WARM_T0 + 2)) instead of 1/gamma.
 WARM_T0 = 50
+# Offset for the small-gamma runs that aim at near-exact equilibration (gamma = 1e-3): there the first
+# steps of the plain schedule (1/gamma = 1000) throw any start far out of the box; eta_1 = 2/(gamma 1e4)
+# = 0.2 keeps the warm start.
+SPREAD_GAMMA = 1e-3
+SPREAD_T0 = 10000
 
 
 def label_matrix(A, *, T=400, k=32, seed=1, gamma=0.0):
@@ -36,6 +42,19 @@ def label_matrix(A, *, T=400, k=32, seed=1, gamma=0.0):
     finally:
         sme.sme_op_destroy(op)
     return X, y
+
+
+def batch_training_set(b, *, T=400, k=32, seed=1, gamma=0.0):
+    """Features and converged (ubar, vbar) of every row and column of a batch (one batched run)."""
+    import torch
+    _, ro, co = sme.sme_batch_get_info(b)
+    M, N = int(ro[-1]), int(co[-1])
+    f32 = dict(dtype=torch.float32, device="cuda")
+    z = [torch.zeros(x, **f32) for x in (M, N, M, N)]
+    sme.sme_batch_equilibrate(b, *z, T=T, k=k, seed=seed, gamma=gamma)
+    X = torch.zeros((M + N, FEATURES), **f32)
+    sme.sme_batch_features(b, seed + 1, X[:M], X[M:])
+    return X, torch.cat([z[2], z[3]])
 
 
 def training_set(mats, **kw):

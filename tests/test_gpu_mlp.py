@@ -180,3 +180,87 @@ def test_warm_start_beats_zero_start_on_held_out_matrices():
             assert warm["rms"] < 2.0 * long["rms"], (i, long, warm)
     finally:
         S.sme_mlp_destroy(mlp)
+
+
+def _batch3():
+    return [I.sparse_variable_row_nnz(300, 200, 0, 12, 31, var=2.0),
+            I.sparse_variable_row_nnz(450, 120, 1, 20, 32, var=2.0),
+            I.sparse_variable_row_nnz(90, 260, 2, 30, 33, var=2.0)]
+
+
+def test_batch_features_match_the_oracle_per_matrix():
+    """Features of a batch: every matrix with its own means and sizes, and matrix b's sketch drawn from its own
+    probe streams (2b for s, 2b + 1 for w)."""
+    mats = _batch3()
+    b = S.sme_batch_create(mats)
+    try:
+        _, ro, co = S.sme_batch_get_info(b)
+        Fr = torch.zeros((int(ro[-1]), 8), dtype=torch.float32, device="cuda")
+        Fc = torch.zeros((int(co[-1]), 8), dtype=torch.float32, device="cuda")
+        S.sme_batch_features(b, 4, Fr, Fc)
+        Fr, Fc = Fr.cpu().double().numpy(), Fc.cpu().double().numpy()
+    finally:
+        S.sme_batch_destroy(b)
+    for i, A in enumerate(mats):
+        fr, fc = Fr[ro[i]:ro[i + 1]], Fc[co[i]:co[i + 1]]
+        z_r = O.row_estimate(A, np.zeros(A.m), np.zeros(A.n), O.probe_signs(4, 1, 2 * i, A.n, 8))
+        z_c = O.col_estimate(A, np.zeros(A.m), np.zeros(A.n), O.probe_signs(4, 1, 2 * i + 1, A.m, 8))
+        f0 = lambda z: 0.5 * np.log(np.maximum(z, 1e-30))
+        for F, z, side in ((fr, z_r, 0.0), (fc, z_c, 1.0)):
+            nz = z > 0
+            np.testing.assert_allclose(F[nz, 0], f0(z[nz]), atol=1e-4)
+            assert np.all(F[:, 3] == side)
+            np.testing.assert_allclose(F[:, 4], f0(z_r).mean(), atol=1e-4)
+            np.testing.assert_allclose(F[:, 5], f0(z_c).mean(), atol=1e-4)
+            np.testing.assert_allclose(F[:, 6], np.log(A.m), rtol=1e-6)
+            np.testing.assert_allclose(F[:, 7], np.log(A.n), rtol=1e-6)
+        nnz_r = np.diff(A.row_ptr)
+        np.testing.assert_allclose(fr[:, 1], np.log1p(nnz_r), atol=1e-6)
+
+
+def test_batch_warm_start_is_the_network_on_the_batch_features():
+    mats = _batch3()
+    b = S.sme_batch_create(mats)
+    mlp = _net(17, np.random.default_rng(17))
+    try:
+        _, ro, co = S.sme_batch_get_info(b)
+        M, N = int(ro[-1]), int(co[-1])
+        F = torch.zeros((M + N, 8), dtype=torch.float32, device="cuda")
+        S.sme_batch_features(b, 6, F[:M], F[M:])
+        y = torch.zeros(M + N, dtype=torch.float32, device="cuda")
+        S.sme_mlp_forward(mlp, F, y)
+        u0 = torch.zeros(M, dtype=torch.float32, device="cuda")
+        v0 = torch.zeros(N, dtype=torch.float32, device="cuda")
+        S.sme_batch_warm_start(b, mlp, 6, u0, v0)
+        assert torch.equal(torch.cat([u0, v0]), y)
+    finally:
+        S.sme_mlp_destroy(mlp)
+        S.sme_batch_destroy(b)
+
+
+def test_batch_evaluate_matches_single_operators():
+    mats = _batch3()
+    b = S.sme_batch_create(mats)
+    rng = np.random.default_rng(3)
+    try:
+        _, ro, co = S.sme_batch_get_info(b)
+        u = rng.normal(0, 0.5, int(ro[-1])).astype(np.float32)
+        v = rng.normal(0, 0.5, int(co[-1])).astype(np.float32)
+        got = S.sme_batch_evaluate(b, torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda(), gamma=0.01)
+    finally:
+        S.sme_batch_destroy(b)
+    for i, A in enumerate(mats):
+        op = S.sme_op_create_csr(A.m, A.n, A.row_ptr, A.col_idx, A.vals.astype(np.float32))
+        try:
+            ref = S.sme_evaluate(op, torch.from_numpy(u[ro[i]:ro[i + 1]]).cuda(),
+                                 torch.from_numpy(v[co[i]:co[i + 1]]).cuda(), gamma=0.01)
+        finally:
+            S.sme_op_destroy(op)
+        for key in ("row_spread", "col_spread", "rms", "objective"):
+            assert got[i][key] == pytest.approx(ref[key], rel=1e-10), (i, key)
+        assert got[i]["empty_rows"] == ref["empty_rows"] and got[i]["empty_cols"] == ref["empty_cols"]
+        # The objective of eq. (3) against the oracle's definition (FP64 on both sides).
+        d = O.default_params(A.m, A.n)
+        f = O.objective(A, u[ro[i]:ro[i + 1]].astype(np.float64), v[co[i]:co[i + 1]].astype(np.float64),
+                        alpha=d["alpha"], beta=d["beta"], gamma=0.01)
+        assert got[i]["objective"] == pytest.approx(f, rel=1e-9)
