@@ -209,8 +209,11 @@ def run_reference(args, rank, world):
 # ------------------------------------------------------------------------------------------ dense workload
 
 def run_dense(args, rank, world, local):
-    """T iterations of Algorithm 1 on a dense 16384^2 BF16 matrix (N(0,1) entries, row and column factors of
-    variance 1.5), k = 256 probes per iteration, on the tensor cores."""
+    """T iterations of Algorithm 1 on a dense 16384^2 matrix (N(0,1) entries, row and column factors of
+    variance 1.5), k = 256 probes per iteration, on the tensor cores: stored in BF16 (the line's value), and
+    as FP8-E4M3 with per-row scales (reported beside it).  For each, the norm spread of the result on the
+    stored matrix (library evaluation) and on the FP64 matrix (NumPy), and a CPU baseline: the FP64 oracle's
+    estimate for a sample of rows and columns at the final state, with the GPU's error on that sample."""
     import numpy as np
     import torch
 
@@ -220,41 +223,98 @@ def run_dense(args, rank, world, local):
     torch.cuda.set_device(local)
     N = max(128, int(round(16384 * args.scale / 128)) * 128)
     k, T = 256, (args.T if args.T != 500 else 300)
-    A = torch.from_numpy(I.dense_badly_scaled(N, N, seed=3 + rank)).to(torch.bfloat16).cuda()
-    op = sme.sme_op_create_dense(N, N, A, dtype=sme.SME_BF16)
-    z = [torch.zeros(N, device="cuda") for _ in range(4)]
-
-    def step():
-        for x in z:
-            x.zero_()
-        sme.sme_equilibrate(op, *z, T=T, k=k, seed=0, flags=sme.SME_EQ_TIMED | sme.SME_EQ_ASYNC)
-
-    for _ in range(args.warmup):
-        step()
-    sme.sme_op_check(op)
-    stream = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    loop_ms = []
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            step()
-            loop_ms.append(sme.sme_op_get_info(op)["last_loop_ms"])
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    sme.sme_op_check(op)
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    iter_s = statistics.mean(loop_ms) / 1e3 / T
+    A64 = I.dense_badly_scaled(N, N, seed=3 + rank)
+    A32 = torch.from_numpy(A64.astype(np.float32))
+    Ab = A32.to(torch.bfloat16).cuda()
+    # FP8-E4M3 with per-row scales: row i stored as A_i / c_i with c_i = max_j |A_ij| / 448.
+    Ag = A32.cuda()
+    scales = (Ag.abs().amax(1) / 448.0).clamp_min(1e-30)
+    codes = (Ag / scales[:, None]).to(torch.float8_e4m3fn).view(torch.uint8).contiguous()
+    del Ag
     peaks, kind = measured_peaks()
-    flops = 2 * 2.0 * N * N * k          # forward and transpose products, algorithmic (one BF16 term)
-    tflops = flops / iter_s / 1e12
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
-    hbm = 2 * 2.0 * N * N / iter_s / 1e9  # A and its transposed copy, read once each per iteration
-    quality = None
+    flops = 2 * 2.0 * N * N * k          # forward and transpose products, algorithmic (one BF16 term)
+
+    def sq_norms_fp64(u, v):
+        """Exact squared row / column norms of D A E on the FP64 matrix (NumPy, in row blocks)."""
+        eu, ev = np.exp(2 * u.astype(np.float64)), np.exp(2 * v.astype(np.float64))
+        r2, c2 = np.zeros(N), np.zeros(N)
+        for i in range(0, N, 1024):
+            B2 = A64[i:i + 1024] ** 2
+            r2[i:i + 1024] = eu[i:i + 1024] * (B2 @ ev)
+            c2 += (eu[i:i + 1024] @ B2) * ev
+        return r2, c2
+
+    def spread(r2, c2):
+        rn, cn = np.sqrt(r2[r2 > 0]), np.sqrt(c2[c2 > 0])
+        return max(rn.max() / rn.min(), cn.max() / cn.min())
+
+    def run(op):
+        z = [torch.zeros(N, device="cuda") for _ in range(4)]
+
+        def step():
+            for x in z:
+                x.zero_()
+            sme.sme_equilibrate(op, *z, T=T, k=k, seed=0, flags=sme.SME_EQ_TIMED | sme.SME_EQ_ASYNC)
+
+        for _ in range(args.warmup):
+            step()
+        sme.sme_op_check(op)
+        stream = torch.cuda.current_stream()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        loop_ms = []
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            ev0.record(stream)
+            for _ in range(args.steps):
+                step()
+                loop_ms.append(sme.sme_op_get_info(op)["last_loop_ms"])
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        sme.sme_op_check(op)
+        elapsed = ev0.elapsed_time(ev1) / 1e3
+        iter_s = statistics.mean(loop_ms) / 1e3 / T
+        q = sme.sme_evaluate(op, z[2], z[3])
+        ub, vb = z[2].cpu().numpy(), z[3].cpu().numpy()
+        r2, c2 = sq_norms_fp64(ub, vb)
+        return {"elapsed": elapsed, "iter_s": iter_s, "clocks": clk.summary(), "ub": ub, "vb": vb,
+                "spread_stored_matrix": max(q["row_spread"], q["col_spread"]), "rms_stored_matrix": q["rms"],
+                "spread_fp64_matrix": spread(r2, c2)}
+
+    op = sme.sme_op_create_dense(N, N, Ab, dtype=sme.SME_BF16)
+    bf = run(op)
+    op8 = sme.sme_op_create_dense(N, N, codes, dtype=sme.SME_FP8E4M3, row_scales=scales)
+    f8 = run(op8)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # The oracle's estimate (k = 256, FP64) for 48 rows and 48 columns at the BF16 run's final state,
+        # on the matrix the tensor cores see, against the library's estimate of the same iteration.
+        import oracle as O
+        rng = np.random.default_rng(5)
+        rows = np.sort(rng.choice(N, 48, replace=False))
+        cols = np.sort(rng.choice(N, 48, replace=False))
+        ub, vb = bf["ub"], bf["vb"]
+        Aseen = Ab.float().cpu().numpy()
+        zu = torch.zeros(N, device="cuda")
+        zv = torch.zeros(N, device="cuda")
+        sme.sme_estimate(op, torch.tensor(ub, device="cuda"), torch.tensor(vb, device="cuda"), T + 1, k, 0, 0, zu, zv)
+        zu, zv = zu.cpu().double().numpy(), zv.cpu().double().numpy()
+        c0 = time.perf_counter()
+        ozu, ozv = O.dense_estimate_sampled(Aseen, ub, vb, rows, cols, t=T + 1, k=k, seed=0)
+        el = time.perf_counter() - c0
+        eu, ev = np.exp(2 * ub.astype(np.float64)), np.exp(2 * vb.astype(np.float64))
+        r2 = eu[rows] * ((Aseen[rows].astype(np.float64) ** 2) @ ev)
+        c2 = ev[cols] * (eu @ (Aseen[:, cols].astype(np.float64) ** 2))
+        err = max(np.max(np.abs(zu[rows] - ozu) / r2), np.max(np.abs(zv[cols] - ozv) / c2))
+        # 96 of 2N rows and columns: that fraction of one iteration's k probe pairs.
+        cpu = {"value": k * (96 / (2 * N)) / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"FP64 estimate (k={k}) of 48 rows + 48 columns of one iteration ({el:.1f} s); "
+                         f"GPU estimate error on that sample: max |dz|/r2 = {err:.2e}"}
+    tflops = flops / bf["iter_s"] / 1e12
     line = {
-        "metric": METRIC, "value": world * k * T * args.steps / elapsed, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "metric": METRIC, "value": world * k * T * args.steps / bf["elapsed"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * bf["elapsed"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": f"dense tensor-core path: A {N}x{N} BF16, entries N(0,1)*exp(N(0,1.5)) row and "
                                f"column factors; k={k} +-1 probes (two-term BF16 scalings), FP32 accumulation; T={T}",
@@ -263,12 +323,20 @@ def run_dense(args, rank, world, local):
                      "traffic": None, "peak_kind": kind + " (bf16 sustained)",
                      "kernel": "dense_iteration<256> (one iteration, both products)",
                      "algorithmic_flops_per_launch": flops, "executed_flops_per_launch": 2 * flops,
-                     "launch_us": iter_s * 1e6, "hbm_gbs": hbm},
-        "gpu_launches": (T + 2) * args.steps, "clocks": clk.summary(),
+                     "launch_us": bf["iter_s"] * 1e6, "hbm_gbs": 2 * 2.0 * N * N / bf["iter_s"] / 1e9},
+        "cpu_baseline": cpu,
+        "quality": {"spread_stored_matrix": bf["spread_stored_matrix"], "spread_fp64_matrix": bf["spread_fp64_matrix"],
+                    "rms_stored_matrix": bf["rms_stored_matrix"]},
+        "fp8": {"storage": "E4M3 codes + per-row FP32 scales (widened exactly to BF16 in the operator)",
+                "launch_us": f8["iter_s"] * 1e6, "probe_pairs_per_s": k * T * args.steps / f8["elapsed"],
+                "spread_stored_matrix": f8["spread_stored_matrix"], "spread_fp64_matrix": f8["spread_fp64_matrix"],
+                "rms_stored_matrix": f8["rms_stored_matrix"], "clocks": f8["clocks"]},
+        "gpu_launches": 2 * (T + 2) * args.steps, "clocks": bf["clocks"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     sme.sme_op_destroy(op)
+    sme.sme_op_destroy(op8)
     return 0
 
 
@@ -283,15 +351,21 @@ def run_batched(args, rank, world, local):
     from paper_1602_06621_gb300 import inputs as I
     from paper_1602_06621_gb300 import sme
 
-    torch.cuda.set_device(local)
+    import scipy.sparse as sps
+
     k, T, count = 16, (args.T if args.T != 500 else 300), 512
     m_hi = max(2000, int(2e5 * args.scale))
-    mats = I.batched_family(count, 1000, m_hi, seed=40 + rank)
+    mats = I.batched_family(count, 1000, m_hi, seed=40 + rank, workers=min(16, os.cpu_count() or 1))
+    torch.cuda.set_device(local)
     b = sme.sme_batch_create(mats)
     _, ro, co = sme.sme_batch_get_info(b)
     M, N = int(ro[-1]), int(co[-1])
     nnz = sum(A.nnz for A in mats)
-    del mats
+    # Right-hand sides b = A x* per matrix (x* ~ N(0,1)) for the per-matrix LSQR solve.
+    rhs = np.concatenate([sps.csr_matrix((A.vals.astype(np.float64), A.col_idx, A.row_ptr), shape=(A.m, A.n))
+                          @ I.normal_vector(A.n, 900 + i, np.float64) for i, A in enumerate(mats)])
+    bvec = torch.tensor(rhs.astype(np.float32), device="cuda")
+    del mats, rhs
     z = [torch.zeros(x, device="cuda") for x in (M, N, M, N)]
     tuned = sme.sme_op_autotune(sme.sme_batch_op(b), k)
 
@@ -321,6 +395,16 @@ def run_batched(args, rank, world, local):
     peak, kind = measured_hbm_peak()
     bytes_iter = algorithmic_bytes_per_iteration(M, N, nnz)
     gbs = bytes_iter / iter_s / 1e9
+    # Per-matrix quality and the per-matrix LSQR solve on the last step's scalings (outside the timed region).
+    ev = sme.sme_batch_evaluate(b, z[2], z[3])
+    spreads = np.array([max(e["row_spread"], e["col_spread"]) for e in ev])
+    x = torch.zeros(N, device="cuda")
+    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0.record(stream)
+    lr = sme.sme_batch_lsqr(b, z[2], z[3], bvec, x, tol=1e-6, max_iters=20000, check_every=10)
+    l1.record(stream)
+    l1.synchronize()
+    its = np.array([r["iters"] for r in lr])
     line = {
         "metric": METRIC, "value": world * count * k * T * args.steps / elapsed, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
@@ -334,6 +418,12 @@ def run_batched(args, rank, world, local):
                      "traffic": None, "peak_kind": kind, "kernel": "sgd_iteration<float,16> over the batch",
                      "algorithmic_bytes_per_launch": bytes_iter, "launch_us": iter_s * 1e6},
         "gpu_launches": (T + 4) * args.steps, "clocks": clk.summary(),
+        "quality": {"spread_median": float(np.median(spreads)), "spread_max": float(spreads.max()),
+                    "rms_median": float(np.median([e["rms"] for e in ev]))},
+        "lsqr": {"ms": l0.elapsed_time(l1), "converged": int(sum(r["converged"] for r in lr)), "of": count,
+                 "iters_median": float(np.median(its)), "iters_p90": float(np.percentile(its, 90)),
+                 "iters_max": int(its.max()), "tol": 1e-6, "iteration_cap": 20000,
+                 "kernel_launches": int(lr[0]["kernel_launches"])},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -56,11 +56,12 @@ __global__ void __launch_bounds__(LQ_THREADS) bl_rows(Sell S, const int32_t *mid
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
     if (slice >= S.nslices) return;
-    const real acc = sell_row_dot<real, real, real>(S, slice, lane, ve);
     const int64_t r = slice * 32 + lane;
-    if (r >= S.rows) return;
+    // Rows of finished matrices (and padding rows) do no work.
+    const bool live = r < S.rows && !sc[mid[r]].done;
+    const real acc = sell_row_dot<real, real, real>(S, slice, lane, ve, live);
+    if (!live) return;
     const BScal &c = sc[mid[r]];
-    if (c.done) return;
     const real inv_alpha = (real)(c.alpha > 0.0 ? 1.0 / c.alpha : 0.0);
     const real inv_beta = (real)(c.beta > 0.0 ? 1.0 / c.beta : 0.0);
     const real dr = d[r];
@@ -77,11 +78,11 @@ __global__ void __launch_bounds__(LQ_THREADS) bl_cols(Sell S, const int32_t *mid
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
     if (slice >= S.nslices) return;
-    const real acc = sell_row_dot<real, real, real>(S, slice, lane, ud);
     const int64_t c = slice * 32 + lane;
-    if (c >= S.rows) return;
+    const bool live = c < S.rows && !sc[mid[c]].done;
+    const real acc = sell_row_dot<real, real, real>(S, slice, lane, ud, live);
+    if (!live) return;
     const BScal &p = sc[mid[c]];
-    if (p.done) return;
     const real inv_alpha = (real)(p.alpha > 0.0 ? 1.0 / p.alpha : 0.0);
     const real inv_beta = (real)(p.beta > 0.0 ? 1.0 / p.beta : 0.0);
     const real ec = e[c];
@@ -181,26 +182,30 @@ __global__ void __launch_bounds__(LQ_THREADS) bl_reduce(const double *sq, const 
 
 template <typename real>
 __global__ void bl_current_x(int64_t N, const int32_t *mid, const int32_t *perm, const real *e, const real *x,
-                             const real *w, const BScal *sc, real *xt, real *x_out)
+                             const real *w, const BScal *sc, real *xt, real *x_out, int skip_done)
 {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     const BScal &p = sc[mid[c]];
+    if (skip_done && p.done == 1) return;
     const real v = e[c] * (x[c] + (real)(p.phi / p.rho) * w[c]);
     xt[c] = v;
     if (x_out) x_out[perm[c]] = v;
 }
 
+// Residual r = A x - b in FP64.  Between checks (skip_done) the rows of matrices that already converged are
+// skipped: their partial sums are not read again before the final pass, which computes every row.
 template <typename real>
-__global__ void __launch_bounds__(LQ_THREADS) bl_residual(Sell S, const real *xt, const real *bs, double *r,
-                                                           double *sq)
+__global__ void __launch_bounds__(LQ_THREADS) bl_residual(Sell S, const int32_t *mid, const BScal *sc, int skip_done,
+                                                           const real *xt, const real *bs, double *r, double *sq)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
     if (slice >= S.nslices) return;
-    const double acc = sell_row_dot<real, double, real>(S, slice, lane, xt);
     const int64_t i = slice * 32 + lane;
-    if (i >= S.rows) return;
+    const bool live = i < S.rows && !(skip_done && sc[mid[i]].done == 1);
+    const double acc = sell_row_dot<real, double, real>(S, slice, lane, xt, live);
+    if (!live) return;
     const double ri = acc - (double)bs[i];
     r[i] = ri;
     sq[S.perm[i]] = ri * ri;
@@ -316,8 +321,8 @@ static sme_status batch_lsqr_t(sme_op op, const real *ubar, const real *vbar, co
             bl_reduce<<<count, LQ_THREADS, 0, s>>>(L->sq_c, nullptr, L->coff, L->sc, RED_ALPHA, p->tol, p->stop_rule, 0);
         }
         it += chunk;
-        bl_current_x<real><<<nblk(N), 256, 0, s>>>(N, mid_c, Bk.perm, e, x, w, L->sc, xt, nullptr);
-        bl_residual<real><<<fb, LQ_THREADS, 0, s>>>(F, xt, bs, L->r, L->sq_r);
+        bl_current_x<real><<<nblk(N), 256, 0, s>>>(N, mid_c, Bk.perm, e, x, w, L->sc, xt, nullptr, 1);
+        bl_residual<real><<<fb, LQ_THREADS, 0, s>>>(F, mid_r, L->sc, 1, xt, bs, L->r, L->sq_r);
         bl_reduce<<<count, LQ_THREADS, 0, s>>>(L->sq_r, nullptr, L->roff, L->sc, RED_RESID, p->tol, p->stop_rule, 0);
         launches += 4 * chunk + 3;
         if (p->stop_rule == 1) {
@@ -331,8 +336,8 @@ static sme_status batch_lsqr_t(sme_op op, const real *ubar, const real *vbar, co
         all_done = true;
         for (int b = 0; b < count; ++b) all_done = all_done && L->host[b].done != 0;
     }
-    bl_current_x<real><<<nblk(N), 256, 0, s>>>(N, mid_c, Bk.perm, e, x, w, L->sc, xt, x_out);
-    bl_residual<real><<<fb, LQ_THREADS, 0, s>>>(F, xt, bs, L->r, L->sq_r);
+    bl_current_x<real><<<nblk(N), 256, 0, s>>>(N, mid_c, Bk.perm, e, x, w, L->sc, xt, x_out, 0);
+    bl_residual<real><<<fb, LQ_THREADS, 0, s>>>(F, mid_r, L->sc, 0, xt, bs, L->r, L->sq_r);
     bl_reduce<<<count, LQ_THREADS, 0, s>>>(L->sq_r, nullptr, L->roff, L->sc, RED_RESID, p->tol, p->stop_rule, 1);
     bl_normal<real><<<bb, LQ_THREADS, 0, s>>>(Bk, L->r, L->sq_c);
     bl_reduce<<<count, LQ_THREADS, 0, s>>>(L->sq_c, nullptr, L->coff, L->sc, RED_NORMAL, p->tol, p->stop_rule, 1);

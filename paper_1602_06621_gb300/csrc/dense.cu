@@ -600,6 +600,53 @@ sme_status dense_equilibrate(sme_op op, const sme_equil_params *p, float *u, flo
     return SME_OK;
 }
 
+// sq[j] = e^{2 x_j} (times c_j^2 when per-row scales are given).
+__global__ void dense_sq(int64_t n, const float *x, const float *scale, double *sq)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double e = exp(2.0 * (double)x[j]);
+    const double c = scale ? (double)scale[j] : 1.0;
+    sq[j] = e * c * c;
+}
+
+// out_i = own_i * sum_j X_ij^2 sq_j for X row-major (rows x cols, cols a multiple of 128), one warp per row,
+// 16-byte loads, FP64 accumulation; own_i = e^{2 x_i} (times c_i^2 for scaled rows).
+__global__ void dense_row_norms(const __nv_bfloat16 *X, int64_t rows, int64_t cols, const double *sq,
+                                const double *own, double *out)
+{
+    const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    const int4 *row = reinterpret_cast<const int4 *>(X + r * cols);
+    double acc = 0.0;
+    for (int64_t q = lane; q < cols / 8; q += 32) {
+        const int4 w = row[q];
+        const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&w);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const double a = (double)__bfloat162float(e[t]);
+            acc += a * a * sq[q * 8 + t];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[r] = own[r] * acc;
+}
+
+sme_status dense_exact_norms(sme_op op, const float *u, const float *v, double *sq_u, double *sq_v, double *r2,
+                             double *c2, cudaStream_t s)
+{
+    DenseOp *D = op->dense;
+    const int64_t m = D->m, n = D->n;
+    dense_sq<<<nblk(m), 256, 0, s>>>(m, u, D->row_scale, sq_u);
+    dense_sq<<<nblk(n), 256, 0, s>>>(n, v, nullptr, sq_v);
+    dense_row_norms<<<nblk(m * 32), 256, 0, s>>>(D->A, m, n, sq_v, sq_u, r2);
+    dense_row_norms<<<nblk(n * 32), 256, 0, s>>>(D->At, n, m, sq_u, sq_v, c2);
+    SME_CUDA(cudaGetLastError());
+    return SME_OK;
+}
+
 sme_status dense_estimate(sme_op op, const float *u, const float *v, int t, int k, uint64_t seed, int sb, float *zu,
                           float *zv, cudaStream_t s)
 {

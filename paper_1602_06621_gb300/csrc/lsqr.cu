@@ -116,29 +116,19 @@ __global__ void eval_partials(int64_t n, const double *r2, const real *x, double
 
 static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// Metrics from exact squared norms r2[m], c2[n] (original order) and the state u, v.
 template <typename real>
-static sme_status evaluate_t(sme_op op, const real *u, const real *v, double alpha, double beta, double gamma,
-                             double *r2_out, double *c2_out, sme_eval_result *res, cudaStream_t s)
+static sme_status evaluate_from_norms(int64_t m, int64_t n, const double *r2, const double *c2, const real *u,
+                                      const real *v, double alpha, double beta, double gamma, sme_eval_result *res,
+                                      EvalPart *parts, cudaStream_t s)
 {
-    const int64_t m = op->m, n = op->n;
-    double *buf = nullptr;
     const int NB = 152;
-    SME_CUDA(cudaMallocAsync((void **)&buf, (size_t)(2 * (m + n)) * sizeof(double) + 2 * NB * sizeof(EvalPart), s));
-    double *sq_u = buf, *sq_v = buf + m, *r2 = buf + m + n, *c2 = buf + 2 * m + n;
-    EvalPart *parts = (EvalPart *)(buf + 2 * (m + n));
-    if (r2_out) r2 = r2_out;
-    if (c2_out) c2 = c2_out;
-    exp2_sorted<real><<<nblk(m), 256, 0, s>>>(m, op->fwd.perm, u, sq_u);
-    exp2_sorted<real><<<nblk(n), 256, 0, s>>>(n, op->bwd.perm, v, sq_v);
-    exact_norms_kernel<real><<<nblk(op->fwd.nslices * 32), 256, 0, s>>>(op->fwd, op->dbl, sq_v, u, r2);
-    exact_norms_kernel<real><<<nblk(op->bwd.nslices * 32), 256, 0, s>>>(op->bwd, op->dbl, sq_u, v, c2);
     eval_partials<real><<<NB, EV_THREADS, 0, s>>>(m, r2, u, alpha, parts);
     eval_partials<real><<<NB, EV_THREADS, 0, s>>>(n, c2, v, beta, parts + NB);
     SME_CUDA(cudaGetLastError());
     std::vector<EvalPart> h(2 * NB);
     SME_CUDA(cudaMemcpyAsync(h.data(), parts, 2 * NB * sizeof(EvalPart), cudaMemcpyDeviceToHost, s));
     SME_CUDA(cudaStreamSynchronize(s));
-    SME_CUDA(cudaFreeAsync(buf, s));
     EvalPart R{0, 0, 0, 0, 0, INFINITY, 0}, C{0, 0, 0, 0, 0, INFINITY, 0};
     for (int b = 0; b < NB; ++b) {
         for (int side = 0; side < 2; ++side) {
@@ -162,6 +152,31 @@ static sme_status evaluate_t(sme_op op, const real *u, const real *v, double alp
     res->empty_rows = (int64_t)R.empty;
     res->empty_cols = (int64_t)C.empty;
     return SME_OK;
+}
+
+template <typename real>
+static sme_status evaluate_t(sme_op op, const real *u, const real *v, double alpha, double beta, double gamma,
+                             double *r2_out, double *c2_out, sme_eval_result *res, cudaStream_t s)
+{
+    const int64_t m = op->m, n = op->n;
+    double *buf = nullptr;
+    const int NB = 152;
+    SME_CUDA(cudaMallocAsync((void **)&buf, (size_t)(2 * (m + n)) * sizeof(double) + 2 * NB * sizeof(EvalPart), s));
+    double *sq_u = buf, *sq_v = buf + m, *r2 = buf + m + n, *c2 = buf + 2 * m + n;
+    EvalPart *parts = (EvalPart *)(buf + 2 * (m + n));
+    if (r2_out) r2 = r2_out;
+    if (c2_out) c2 = c2_out;
+    if (op->dense) {
+        SME_TRY(dense_exact_norms(op, (const float *)u, (const float *)v, sq_u, sq_v, r2, c2, s));
+    } else {
+        exp2_sorted<real><<<nblk(m), 256, 0, s>>>(m, op->fwd.perm, u, sq_u);
+        exp2_sorted<real><<<nblk(n), 256, 0, s>>>(n, op->bwd.perm, v, sq_v);
+        exact_norms_kernel<real><<<nblk(op->fwd.nslices * 32), 256, 0, s>>>(op->fwd, op->dbl, sq_v, u, r2);
+        exact_norms_kernel<real><<<nblk(op->bwd.nslices * 32), 256, 0, s>>>(op->bwd, op->dbl, sq_u, v, c2);
+    }
+    const sme_status st = evaluate_from_norms<real>(m, n, r2, c2, u, v, alpha, beta, gamma, res, parts, s);
+    cudaFreeAsync(buf, s);
+    return st;
 }
 
 // Per-matrix partials of a batch: block (b, side) reduces matrix b's rows (side 0) or columns (side 1), whose
@@ -711,10 +726,6 @@ extern "C" sme_status sme_evaluate(sme_op op, const void *u, const void *v, doub
     if (!op || !u || !v || !res) {
         set_error("sme_evaluate: bad arguments");
         return SME_ERR_ARG;
-    }
-    if (op->dense) {
-        set_error("sme_evaluate: dense operators are evaluated through sme_estimate");
-        return SME_ERR_UNSUPPORTED;
     }
     if (alpha <= 0) alpha = std::pow((double)op->n / (double)op->m, 0.25);
     if (beta <= 0) beta = std::pow((double)op->m / (double)op->n, 0.25);

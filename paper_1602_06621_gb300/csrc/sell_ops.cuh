@@ -53,9 +53,10 @@ __device__ __forceinline__ void pair_load(const Sell &S, int64_t pi, int &c0, re
 
 // sum_l a_l * g[c_l] over the row owned by this thread (acc type `acc_t`), software-pipelined.
 template <typename real, typename acc_t, typename G>
-__device__ __forceinline__ acc_t sell_row_dot(const Sell &S, int64_t slice, int lane, const G *g)
+__device__ __forceinline__ acc_t sell_row_dot(const Sell &S, int64_t slice, int lane, const G *g, bool active = true)
 {
-    const int np = S.slice_w[slice] / 2;
+    // An inactive lane loads nothing and returns 0 (its row belongs to a finished problem).
+    const int np = active ? S.slice_w[slice] / 2 : 0;
     const int64_t pbase = S.slice_off[slice] / 2 + lane;
     acc_t acc = acc_t(0);
     int c0 = 0, c1 = 0, n0 = 0, n1 = 0;

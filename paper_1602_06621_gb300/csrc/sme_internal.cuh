@@ -194,6 +194,9 @@ void release_lsqr(sme_op op);
 void dense_destroy(sme_op op);
 sme_status dense_equilibrate(sme_op op, const sme_equil_params *p, float *u, float *v, float *ub, float *vb,
                              cudaStream_t s);
+// Exact squared row / column norms of D A E (FP64 accumulation) for a dense operator; sq_u[m], sq_v[n] scratch.
+sme_status dense_exact_norms(sme_op op, const float *u, const float *v, double *sq_u, double *sq_v, double *r2,
+                             double *c2, cudaStream_t s);
 sme_status dense_estimate(sme_op op, const float *u, const float *v, int t, int k, uint64_t seed, int sb,
                           float *zu, float *zv, cudaStream_t s);
 

@@ -181,3 +181,45 @@ def test_dense_argument_errors():
     with pytest.raises(sme.SmeError) as ei:
         sme.sme_op_create_dense(256, 256, A, dtype=sme.SME_BF16)
     assert ei.value.name == "SME_ERR_NONFINITE"
+
+
+@pytest.mark.parametrize("fp8", [False, True])
+def test_dense_evaluate_matches_oracle(fp8):
+    """sme_evaluate on a dense operator: exact norms of D A E (FP64 accumulation) and the metrics built from
+    them, against the oracle's exact norms and objective on the dequantised matrix."""
+    import torch
+    m, n = 384, 256
+    rng = np.random.default_rng(21)
+    scales = None
+    if fp8:
+        codes = rng.integers(0, 256, size=(m, n)).astype(np.uint8)
+        codes[(codes & 0x7F) == 0x7F] = 0x38
+        scales = np.exp(rng.normal(0, 1.0, m)).astype(np.float32)
+        Af = _e4m3_values()[codes]
+        op = sme.sme_op_create_dense(m, n, torch.tensor(codes, device="cuda"), dtype=sme.SME_FP8E4M3,
+                                     row_scales=torch.tensor(scales, device="cuda"))
+        Aeff = Af * scales.astype(np.float64)[:, None]
+    else:
+        Ad, Af = _bf16_matrix(m, n, 22)
+        op = sme.sme_op_create_dense(m, n, Ad, dtype=sme.SME_BF16)
+        Aeff = Af.astype(np.float64)
+    try:
+        u = rng.normal(0, 0.5, m).astype(np.float32)
+        v = rng.normal(0, 0.5, n).astype(np.float32)
+        r2 = torch.zeros(m, dtype=torch.float64, device="cuda")
+        c2 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        got = sme.sme_evaluate(op, torch.tensor(u, device="cuda"), torch.tensor(v, device="cuda"), gamma=0.05,
+                               r2=r2, c2=c2)
+        r2, c2 = r2.cpu().numpy(), c2.cpu().numpy()
+    finally:
+        sme.sme_op_destroy(op)
+    er2, ec2 = O.exact_norms_sq(Aeff, u.astype(np.float64), v.astype(np.float64))
+    np.testing.assert_allclose(r2, er2, rtol=1e-12)
+    np.testing.assert_allclose(c2, ec2, rtol=1e-12)
+    d = O.default_params(m, n)
+    f = O.objective(Aeff, u.astype(np.float64), v.astype(np.float64), alpha=d["alpha"], beta=d["beta"], gamma=0.05)
+    assert got["objective"] == pytest.approx(f, rel=1e-10)
+    rn, cn = np.sqrt(er2[er2 > 0]), np.sqrt(ec2[ec2 > 0])
+    assert got["row_spread"] == pytest.approx(rn.max() / rn.min(), rel=1e-10)
+    assert got["col_spread"] == pytest.approx(cn.max() / cn.min(), rel=1e-10)
+    assert got["rms"] == pytest.approx(O.rms_error(er2, ec2, d["alpha"], d["beta"]), rel=1e-10)
