@@ -6,3 +6,4 @@ the CUDA library; the two meet only through the seeded input generators and
 the published Philox definition that each side implements on its own.
 """
 from .oracle import *  # noqa: F401,F403
+from . import ccp, mlp  # noqa: F401
