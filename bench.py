@@ -49,10 +49,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lsqr", action="store_true")
-    ap.add_argument("--workload", choices=["large", "dense", "batched", "learned"], default="large",
+    ap.add_argument("--workload", choices=["large", "dense", "batched", "learned", "ccp"], default="large",
                     help="large: the sparse 1e6 x 5e5 step (default); dense: 16384^2 BF16 tensor-core step; "
                          "batched: 512 matrices of uneven size in one operator; learned: warm start vs zero "
-                         "start to a norm spread of 1.05 on 500 held-out matrices")
+                         "start to a norm spread of 1.05 on 500 held-out matrices; ccp: the Lasso of Section 5.2 "
+                         "by Chambolle-Cremers-Pock with and without equilibration")
     return ap.parse_args()
 
 
@@ -593,6 +594,91 @@ def run_learned(args, rank, world, local):
     return 0
 
 
+def run_ccp(args, rank, world, local):
+    """Section 5.2's experiment: A as in Section 4 (1% uniform-random nonzeros, N(0,1) values, row and column
+    factors e^{N(1,1)}) with m = 1e4, n = 2e4; x_hat with n/10 N(0,1) nonzeros, b = A x_hat + N(0,1) noise,
+    lam = 1e-3 ||A^T b||_inf.  CCP (FP32 vectors, FP64 objective checks) without equilibration and after
+    T = 10, 30, 100, 300 iterations of Algorithm 1 (one probe pair, the paper's parameters), each to a relative
+    gap (f - p*)/f(0) <= 1e-6, iterations counted with the equilibration iterations as in the paper.  p* comes
+    from a long FP64 run of the same solver (20000 iterations after 300 equilibration iterations)."""
+    import numpy as np
+    import scipy.sparse as sps
+    import torch
+
+    from paper_1602_06621_gb300 import inputs as I
+    from paper_1602_06621_gb300 import sme
+
+    torch.cuda.set_device(local)
+    m, n = max(100, int(1e4 * args.scale)), max(200, int(2e4 * args.scale))
+    A = I.sparse_uniform_density(m, n, 0.01, seed=11 + rank, mean=1.0, var=1.0, dtype=np.float64)
+    rng = np.random.default_rng(12 + rank)
+    xh = np.zeros(n)
+    idx = rng.choice(n, n // 10, replace=False)
+    xh[idx] = rng.standard_normal(idx.size)
+    S = sps.csr_matrix((A.vals, A.col_idx, A.row_ptr), shape=(m, n))
+    b = S @ xh + rng.standard_normal(m)
+    lam = 1e-3 * float(np.abs(S.T @ b).max())
+    op64 = sme.sme_op_create_csr(m, n, A.row_ptr, A.col_idx, A.vals)
+    op = sme.sme_op_create_csr(m, n, A.row_ptr, A.col_idx, A.vals.astype(np.float32))
+    f64 = dict(dtype=torch.float64, device="cuda")
+    f32 = dict(dtype=torch.float32, device="cuda")
+    b64, b32 = torch.tensor(b, **f64), torch.tensor(b, **f32)
+
+    def equilibrate(o, T, kw):
+        z = [torch.zeros(x, **kw) for x in (m, n, m, n)]
+        if T > 0:
+            sme.sme_equilibrate(o, *z, T=T, k=1, seed=0)
+            return z[2], z[3]
+        return None, None
+
+    # p*: long FP64 run.
+    u64, v64 = equilibrate(op64, 300, f64)
+    xs = torch.zeros(n, **f64)
+    long_res, long_hist = sme.sme_ccp_lasso(op64, u64, v64, b64, xs, lam=lam, max_iters=20000, check_every=1000)
+    pstar = min(long_hist + [long_res["objective"]])
+    drift = (long_hist[-6] - long_hist[-1]) / long_res["objective0"] if len(long_hist) > 6 else None
+    arms = {}
+    for T in (0, 10, 30, 100, 300):
+        def run():
+            ub, vb = equilibrate(op, T, f32)
+            x = torch.zeros(n, **f32)
+            return sme.sme_ccp_lasso(op, ub, vb, b32, x, lam=lam, max_iters=20000, check_every=10, p_star=pstar,
+                                     tol=1e-6, history=False)[0]
+        for _ in range(args.warmup):
+            run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(torch.cuda.current_stream())
+        for _ in range(args.steps):
+            res = run()
+        e1.record(torch.cuda.current_stream())
+        e1.synchronize()
+        arms[f"T={T}"] = {"ccp_iters": int(res["iters"]), "total_iters": int(res["iters"]) + T,
+                          "converged": bool(res["converged"]), "rel_gap": res["rel_gap"],
+                          "op_norm": res["op_norm"], "ms": e0.elapsed_time(e1) / args.steps}
+    best = min((a["total_iters"] for k, a in arms.items() if k != "T=0" and a["converged"]), default=None)
+    line = {
+        "metric": "CCP (Section 5.2) iterations and wall-time to a relative Lasso gap of 1e-6, with and without "
+                  "equilibration",
+        "value": arms["T=100"]["ms"], "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"Lasso of Section 5.2: A {m}x{n}, 1% uniform-random nonzeros, N(0,1) values, "
+                               f"row/column factors e^N(1,1); b = A x_hat + noise; lam = 1e-3 ||A^T b||_inf; "
+                               f"Algorithm 1 with k=1, gamma=0.1",
+                   "m": m, "n": n, "nnz": A.nnz, "lambda": lam,
+                   "l2": "small problem (L2-resident): latency-bound, not a bandwidth figure"},
+        "p_star": pstar, "p_star_drift_last_5000_iters": drift, "arms": arms,
+        "speedup_iters_T100": (arms["T=0"]["total_iters"] / arms["T=100"]["total_iters"]
+                               if arms["T=0"]["converged"] and arms["T=100"]["converged"] else None),
+        "best_total_iters_with_equilibration": best,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sme.sme_op_destroy(op)
+    sme.sme_op_destroy(op64)
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -606,6 +692,8 @@ def main():
         return run_batched(args, rank, world, local)
     if args.workload == "learned":
         return run_learned(args, rank, world, local)
+    if args.workload == "ccp":
+        return run_ccp(args, rank, world, local)
 
     import numpy as np
     import torch

@@ -319,6 +319,50 @@ sme_status sme_batch_op(sme_batch b, sme_op *op);
 sme_status sme_batch_evaluate(sme_batch b, const void *u, const void *v, double alpha, double beta, double gamma,
                               sme_eval_result *res, void *stream);
 
+/* ------------------------------------------------------------------ Chambolle-Cremers-Pock (Section 5.2) */
+
+/*
+ * sme_op_norm2 -- ||D A E||_2 by `iters` steps of power iteration on K^T K (K = D A E), started at the unit
+ * vector 1/sqrt(n); returns sqrt(||K^T K p||) for the last unit iterate p in *norm (host).  u_bar, v_bar
+ * (state type, device) may be NULL for D = I or E = I.  Single sparse operators only.  Synchronises.
+ */
+sme_status sme_op_norm2(sme_op op, const void *u_bar, const void *v_bar, int32_t iters, double *norm, void *stream);
+
+typedef struct {
+    double lambda;       /* > 0: the Lasso weight; the paper uses 1e-3 ||A^T b||_inf */
+    double tau, sigma;   /* primal / dual steps; <= 0 selects 0.9 / ||D A E||_2 (Section 5.2) */
+    double theta;        /* extrapolation; <= 0 selects 1 */
+    int64_t max_iters;
+    int32_t check_every; /* the objective is evaluated (FP64, original system) every check_every iterations */
+    int32_t norm_iters;  /* power iterations for ||D A E||_2 when a step is selected; <= 0 selects 100 */
+    double p_star;       /* known optimal value (> 0), for the stopping rule; <= 0: run max_iters */
+    double tol;          /* stop at the first check with (f(x) - p_star) / f(0) <= tol */
+} sme_ccp_params;
+
+typedef struct {
+    int64_t iters;        /* iterations done */
+    double objective;     /* f(x) at the returned x */
+    double objective0;    /* f(0) = ||b||^2 / sqrt(lambda) */
+    double rel_gap;       /* (f(x) - p_star) / f(0), NaN without p_star */
+    double op_norm;       /* ||D A E||_2 used for the steps (0 when both steps were given) */
+    double tau, sigma;    /* the steps used */
+    int32_t converged;    /* 1 when rel_gap <= tol */
+    int64_t kernel_launches;
+    int64_t history_count; /* entries written to history */
+} sme_ccp_result;
+
+/*
+ * sme_ccp_lasso -- the Lasso problem of Section 5.2,
+ *     minimize ||A x - b||^2 / sqrt(lambda) + sqrt(lambda) ||x||_1,
+ * by the Chambolle-Cremers-Pock primal-dual method on the equilibrated operator D A E (x = E xs), all
+ * iterates starting at 0.  u_bar, v_bar: the log-scalings (device, state type; NULL for no scaling on that
+ * side).  b[m] (device) and x[n] (device, output, original variables).  history (host, may be NULL): f(x)
+ * at every check, up to history_cap entries.  Single sparse operators only.  Synchronises.
+ */
+sme_status sme_ccp_lasso(sme_op op, const void *u_bar, const void *v_bar, const void *b, void *x,
+                         const sme_ccp_params *p, sme_ccp_result *res, double *history, int64_t history_cap,
+                         void *stream);
+
 /* ------------------------------------------------------------------ learned warm start */
 
 /*

@@ -321,36 +321,6 @@ struct LsqrState {
 
 
 
-// Writes this block's partial, and returns true in every thread of the block that arrives last.
-__device__ __forceinline__ bool arrive_last(double part, double *partials, unsigned *counter)
-{
-    __shared__ bool last;
-    const double b = block_sum(part);
-    if (threadIdx.x == 0) {
-        partials[blockIdx.x] = b;
-        __threadfence();
-        last = atomicAdd(counter, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    return last;
-}
-
-// In the last block: the sum of all partials in a fixed order (deterministic).
-__device__ __forceinline__ double sum_partials(const double *partials, unsigned *counter)
-{
-    __threadfence();
-    double v = 0.0;
-    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) v += ((volatile const double *)partials)[i];
-    const double s = block_sum(v);
-    __shared__ double res;
-    if (threadIdx.x == 0) {
-        res = s;
-        *counter = 0u;
-    }
-    __syncthreads();
-    return res;
-}
-
 // b in sorted row order, u_1 = D b / beta_1 stored as ud = D (D b); beta_1 and ||b|| reduced.
 template <typename real>
 __global__ void lsqr_init_rows(int64_t m, const int32_t *perm, const real *b, const real *d, real *bs, real *ud,

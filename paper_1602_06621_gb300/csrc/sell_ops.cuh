@@ -1,4 +1,5 @@
-// Device helpers shared by the LSQR and evaluation kernels: FP64 block sums and the software-pipelined
+// Device helpers shared by the LSQR, CCP and evaluation kernels: FP64 block sums, deterministic grid
+// reductions (the last block to arrive sums the block partials in block order), and the software-pipelined
 // dot product of one sliced-ELL row with a gathered vector.
 #pragma once
 
@@ -30,6 +31,36 @@ __device__ __forceinline__ double block_sum(double v)
         t = warp_sum(t);
     }
     return t;
+}
+
+// Writes this block's partial, and returns true in every thread of the block that arrives last.
+__device__ __forceinline__ bool arrive_last(double part, double *partials, unsigned *counter)
+{
+    __shared__ bool last;
+    const double b = block_sum(part);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = b;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    return last;
+}
+
+// In the last block: the sum of all partials in a fixed order (deterministic).
+__device__ __forceinline__ double sum_partials(const double *partials, unsigned *counter)
+{
+    __threadfence();
+    double v = 0.0;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) v += ((volatile const double *)partials)[i];
+    const double s = block_sum(v);
+    __shared__ double res;
+    if (threadIdx.x == 0) {
+        res = s;
+        *counter = 0u;
+    }
+    __syncthreads();
+    return res;
 }
 
 template <typename real>

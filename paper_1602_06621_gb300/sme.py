@@ -23,7 +23,7 @@ __all__ = [
     "sme_equilibrate_targets", "sme_equilibrate_symmetric", "sme_equilibrate_block", "sme_mlp_create",
     "sme_mlp_destroy", "sme_mlp_param_count", "sme_mlp_get_params", "sme_mlp_set_params", "sme_mlp_forward",
     "sme_mlp_gradient", "sme_mlp_train_step", "sme_op_features", "sme_warm_start", "sme_batch_evaluate",
-    "sme_batch_features", "sme_batch_warm_start",
+    "sme_batch_features", "sme_batch_warm_start", "sme_op_norm2", "sme_ccp_lasso",
 ]
 SME_STATIC_MAX_COLS = 1 << 20
 
@@ -57,6 +57,19 @@ class sme_op_info(ctypes.Structure):
 class sme_eval_result(ctypes.Structure):
     _fields_ = [("row_spread", ctypes.c_double), ("col_spread", ctypes.c_double), ("rms", ctypes.c_double),
                 ("objective", ctypes.c_double), ("empty_rows", ctypes.c_int64), ("empty_cols", ctypes.c_int64)]
+
+
+class sme_ccp_params(ctypes.Structure):
+    _fields_ = [("lam", ctypes.c_double), ("tau", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("theta", ctypes.c_double), ("max_iters", ctypes.c_int64), ("check_every", ctypes.c_int32),
+                ("norm_iters", ctypes.c_int32), ("p_star", ctypes.c_double), ("tol", ctypes.c_double)]
+
+
+class sme_ccp_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("objective", ctypes.c_double), ("objective0", ctypes.c_double),
+                ("rel_gap", ctypes.c_double), ("op_norm", ctypes.c_double), ("tau", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("converged", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
+                ("history_count", ctypes.c_int64)]
 
 
 class sme_lsqr_params(ctypes.Structure):
@@ -114,6 +127,8 @@ SIGNATURES = {
     "sme_batch_evaluate": ([_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp, _vp], _i32),
     "sme_batch_features": ([_vp, _u64, _vp, _vp, _vp], _i32),
     "sme_batch_warm_start": ([_vp, _vp, _u64, _vp, _vp, _vp], _i32),
+    "sme_op_norm2": ([_vp, _vp, _vp, _i32, ctypes.POINTER(ctypes.c_double), _vp], _i32),
+    "sme_ccp_lasso": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp], _i32),
 }
 
 
@@ -434,3 +449,24 @@ def sme_batch_features(b, seed, row_features, col_features, stream=None):
 def sme_batch_warm_start(b, mlp, seed, u0, v0, stream=None):
     _check(load().sme_batch_warm_start(b, mlp, int(seed), _ptr(u0), _ptr(v0), _stream(stream)),
            "sme_batch_warm_start")
+
+
+def sme_op_norm2(op, u_bar=None, v_bar=None, iters=100, stream=None) -> float:
+    out = ctypes.c_double()
+    _check(load().sme_op_norm2(op, _ptr(u_bar), _ptr(v_bar), int(iters), ctypes.byref(out), _stream(stream)),
+           "sme_op_norm2")
+    return out.value
+
+
+def sme_ccp_lasso(op, u_bar, v_bar, b, x, *, lam, max_iters, check_every=10, tau=0.0, sigma=0.0, theta=0.0,
+                  norm_iters=0, p_star=0.0, tol=0.0, history=True, stream=None):
+    """Section 5.2's Lasso by Chambolle-Cremers-Pock; returns (result dict, objective history list)."""
+    p = sme_ccp_params(float(lam), float(tau), float(sigma), float(theta), int(max_iters), int(check_every),
+                       int(norm_iters), float(p_star), float(tol))
+    res = sme_ccp_result()
+    cap = (int(max_iters) // max(1, int(check_every)) + 2) if history else 0
+    hist = np.zeros(max(cap, 1))
+    _check(load().sme_ccp_lasso(op, _ptr(u_bar), _ptr(v_bar), _ptr(b), _ptr(x), ctypes.byref(p), ctypes.byref(res),
+                                _ptr(hist) if cap else None, cap, _stream(stream)), "sme_ccp_lasso")
+    out = {f: getattr(res, f) for f, _ in sme_ccp_result._fields_}
+    return out, list(hist[:res.history_count])
