@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "sme_internal.cuh"
@@ -60,7 +61,35 @@ static void free_sell(sme_op op, Sell &S)
     (void)op;
 }
 
-// Host-side CSR validation (for host input), mirrors the device check.
+// Host-side CSR validation (for host input), mirrors the device check.  Rows are checked in parallel
+// chunks (threads only for large inputs); the error reported is the one of the lowest failing row.
+template <typename real>
+static void validate_rows(int64_t r0, int64_t r1, int64_t n, const int32_t *rp, const int32_t *col, const real *val,
+                          int64_t *bad_row, int *bad_kind)
+{
+    for (int64_t i = r0; i < r1; ++i) {
+        if (rp[i + 1] < rp[i]) {
+            *bad_row = i;
+            *bad_kind = 1;
+            return;
+        }
+        int32_t prev = -1;
+        for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
+            if (col[q] <= prev || col[q] >= n) {
+                *bad_row = i;
+                *bad_kind = 2;
+                return;
+            }
+            prev = col[q];
+            if (!std::isfinite((double)val[q])) {
+                *bad_row = i;
+                *bad_kind = 3;
+                return;
+            }
+        }
+    }
+}
+
 template <typename real>
 static sme_status validate_host(int64_t m, int64_t n, int64_t nnz, const int32_t *rp, const int32_t *col,
                                 const real *val)
@@ -69,23 +98,33 @@ static sme_status validate_host(int64_t m, int64_t n, int64_t nnz, const int32_t
         set_error("row_ptr must start at 0 and end at nnz");
         return SME_ERR_INVALID_CSR;
     }
-    for (int64_t i = 0; i < m; ++i) {
-        if (rp[i + 1] < rp[i]) {
-            set_error("row_ptr decreases at row %lld", (long long)i);
+    // row_ptr must stay within [0, nnz] before any thread follows it.
+    for (int64_t i = 0; i <= m; ++i)
+        if (rp[i] < 0 || rp[i] > nnz) {
+            set_error("row_ptr out of range at row %lld", (long long)i);
             return SME_ERR_INVALID_CSR;
         }
-        int32_t prev = -1;
-        for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
-            if (col[q] <= prev || col[q] >= n) {
-                set_error("column index out of range or not increasing in row %lld", (long long)i);
-                return SME_ERR_INVALID_CSR;
-            }
-            prev = col[q];
-            if (!std::isfinite((double)val[q])) {
-                set_error("non-finite value at nonzero %lld", (long long)q);
-                return SME_ERR_NONFINITE;
-            }
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nt = nnz < (1 << 20) ? 1 : (int)std::min<unsigned>(16u, hw);
+    std::vector<int64_t> bad_row(nt, -1);
+    std::vector<int> bad_kind(nt, 0);
+    if (nt == 1) {
+        validate_rows<real>(0, m, n, rp, col, val, &bad_row[0], &bad_kind[0]);
+    } else {
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; ++t) {
+            const int64_t r0 = m * t / nt, r1 = m * (t + 1) / nt;
+            th.emplace_back(validate_rows<real>, r0, r1, n, rp, col, val, &bad_row[t], &bad_kind[t]);
         }
+        for (auto &t : th) t.join();
+    }
+    for (int t = 0; t < nt; ++t) {
+        if (bad_row[t] < 0) continue;
+        const long long i = (long long)bad_row[t];
+        if (bad_kind[t] == 1) set_error("row_ptr decreases at row %lld", i);
+        if (bad_kind[t] == 2) set_error("column index out of range or not increasing in row %lld", i);
+        if (bad_kind[t] == 3) set_error("non-finite value in row %lld", i);
+        return bad_kind[t] == 3 ? SME_ERR_NONFINITE : SME_ERR_INVALID_CSR;
     }
     return SME_OK;
 }
