@@ -35,6 +35,17 @@ FALLBACK_HBM_GBS = 6800.0
 # The iteration kernel's sources: recorded ncu traffic is used only while these are unchanged.
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1602_06621_gb300", "csrc", f) for f in ("equilibrate.cu", "sme_internal.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sgd_iteration_f32_k32_large.txt")
+# Random 8-byte gathers per second from L2-resident tables, measured on GB300 by
+# paper_1602_06621_gb300/microbench/gather_ceiling.cu (profiles/sgd_iteration_f32_k32_large.txt): the second
+# ceiling of the sparse kernels, which gather one table entry per nonzero per pass.
+GATHER_CEILING_PER_S = 2.93e11
+
+
+def gather_roofline(nnz, launch_s):
+    """The gather ceiling beside the HBM roofline: 2 nnz gathers per iteration (one per pass)."""
+    g = 2.0 * nnz
+    return {"gathers_per_launch": g, "achieved_per_s": g / launch_s, "peak_per_s": GATHER_CEILING_PER_S,
+            "frac": g / launch_s / GATHER_CEILING_PER_S, "peak_kind": "measured (gather_ceiling.cu)"}
 
 
 def parse():
@@ -417,7 +428,7 @@ def run_batched(args, rank, world, local):
                    "launch_shape": tuned, "l2": f"inputs larger than L2 ({16 * nnz / 1e6:.0f} MB per iteration)"},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                      "traffic": None, "peak_kind": kind, "kernel": "sgd_iteration<float,16> over the batch",
-                     "algorithmic_bytes_per_launch": bytes_iter, "launch_us": iter_s * 1e6},
+                     "algorithmic_bytes_per_launch": bytes_iter, "launch_us": iter_s * 1e6, "gather_ceiling": gather_roofline(nnz, iter_s)},
         "gpu_launches": (T + 4) * args.steps, "clocks": clk.summary(),
         "quality": {"spread_median": float(np.median(spreads)), "spread_max": float(spreads.max()),
                     "rms_median": float(np.median([e["rms"] for e in ev]))},
@@ -854,7 +865,8 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": recorded_traffic(), "peak_kind": peak_kind,
                          "kernel": "sgd_iteration<float,32> (one iteration of Algorithm 1, both passes)",
-                         "algorithmic_bytes_per_launch": bytes_iter, "launch_us": iter_s * 1e6},
+                         "algorithmic_bytes_per_launch": bytes_iter, "launch_us": iter_s * 1e6,
+                         "gather_ceiling": gather_roofline(nnz, iter_s)},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": gpu_launches,

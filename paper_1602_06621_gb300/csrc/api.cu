@@ -191,6 +191,14 @@ extern "C" sme_status sme_op_create_csr(sme_op *out, int64_t m, int64_t n, int64
                                         const int32_t *col_idx, const void *vals, sme_dtype dtype, int on_device,
                                         void *stream)
 {
+    return create_csr_grouped(out, m, n, nnz, row_ptr, col_idx, vals, dtype, on_device, stream, nullptr, nullptr, 0);
+}
+
+sme_status sme::create_csr_grouped(sme_op *out, int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr,
+                                   const int32_t *col_idx, const void *vals, sme_dtype dtype, int on_device,
+                                   void *stream, const uint32_t *row_group_host, const uint32_t *col_group_host,
+                                   int group_bits)
+{
     if (!out) return SME_ERR_ARG;
     *out = nullptr;
     if (m < 1 || n < 1 || nnz < 0 || nnz > 0x7fffffffLL - 64 || m > 0x7fffffffLL || n > 0x7fffffffLL || !row_ptr ||
@@ -244,9 +252,26 @@ extern "C" sme_status sme_op_create_csr(sme_op *out, int64_t m, int64_t n, int64
         d_col = (const int32_t *)tmp[1];
         d_val = tmp[2];
     }
-    st = build_sparse(op, d_rp, d_col, d_val, s);
+    uint32_t *groups[2] = {nullptr, nullptr};
+    if (row_group_host && col_group_host) {
+        const int64_t len[2] = {m, n};
+        const uint32_t *src[2] = {row_group_host, col_group_host};
+        for (int i = 0; i < 2; ++i) {
+            if (cudaMalloc(&groups[i], (size_t)len[i] * 4) != cudaSuccess) {
+                // Without room for the ids the build proceeds ungrouped (same results, other order).
+                cudaGetLastError();
+                if (groups[0]) cudaFree(groups[0]);
+                groups[0] = groups[1] = nullptr;
+                break;
+            }
+            cudaMemcpyAsync(groups[i], src[i], (size_t)len[i] * 4, cudaMemcpyHostToDevice, s);
+        }
+    }
+    st = build_sparse(op, d_rp, d_col, d_val, s, groups[0], groups[1], groups[0] && groups[1] ? group_bits : 0);
     cudaStreamSynchronize(s);
     for (void *p : tmp)
+        if (p) cudaFree(p);
+    for (void *p : groups)
         if (p) cudaFree(p);
     if (st != SME_OK) {
         sme_op_destroy(op);

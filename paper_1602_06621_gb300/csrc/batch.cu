@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -96,8 +97,35 @@ extern "C" sme_status sme_batch_create(sme_batch *out, int32_t count, const int6
         }
     }
     rp[M] = (int32_t)NNZ;
+    // Matrices are grouped in order so that each group's gather tables (8 bytes per row and per column) stay
+    // within L2_GROUP_BYTES; rows and columns are then laid out group-major, so the CTAs running at any
+    // moment gather from one group's tables and those stay L2-resident (one group per matrix when a single
+    // matrix is larger).
+    // SME_BATCH_GROUP_BYTES overrides the budget (tests use a small one to exercise grouping).
+    int64_t L2_GROUP_BYTES = 32ll << 20;
+    if (const char *env = std::getenv("SME_BATCH_GROUP_BYTES")) {
+        const long long v = std::atoll(env);
+        if (v > 0) L2_GROUP_BYTES = v;
+    }
+    std::vector<uint32_t> gr(M), gc(N);
+    uint32_t g = 0;
+    int64_t acc = 0;
+    for (int32_t b = 0; b < count; ++b) {
+        const int64_t bytes = 8 * (m[b] + n[b]);
+        if (acc > 0 && acc + bytes > L2_GROUP_BYTES) {
+            ++g;
+            acc = 0;
+        }
+        acc += bytes;
+        for (int64_t i = roff[b]; i < roff[b + 1]; ++i) gr[i] = g;
+        for (int64_t j = coff[b]; j < coff[b + 1]; ++j) gc[j] = g;
+    }
+    int gbits = 0;
+    while ((1u << gbits) <= g) ++gbits;
     sme_op op = nullptr;
-    sme_status st = sme_op_create_csr(&op, M, N, NNZ, rp.data(), ci.data(), va.data(), dtype, 0, stream);
+    sme_status st = g > 0 ? create_csr_grouped(&op, M, N, NNZ, rp.data(), ci.data(), va.data(), dtype, 0, stream,
+                                               gr.data(), gc.data(), gbits)
+                          : sme_op_create_csr(&op, M, N, NNZ, rp.data(), ci.data(), va.data(), dtype, 0, stream);
     if (st != SME_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     BatchInfo *B = new BatchInfo();

@@ -298,11 +298,14 @@ __global__ void max_i32(const int32_t *x, int64_t n, int *out)
 }
 
 // Sort keys that put longer rows first: key = maxlen - len.
-__global__ void length_keys(const int32_t *len, int64_t n, int maxlen, uint32_t *k, int32_t *v)
+// Sort keys: descending length, optionally after an ascending group id in the high bits (group-major).
+__global__ void length_keys(const int32_t *len, int64_t n, int maxlen, const uint32_t *group, int len_bits,
+                            uint32_t *k, int32_t *v)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    k[i] = (uint32_t)(maxlen - len[i]);
+    const uint32_t key = (uint32_t)(maxlen - len[i]);
+    k[i] = group ? (group[i] << len_bits) | key : key;
     v[i] = (int32_t)i;
 }
 
@@ -321,7 +324,10 @@ __global__ void slice_sizes(const int32_t *len_sorted, int64_t rows, int64_t nsl
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nslices) return;
-    int w = len_sorted[s * 32];  // longest row of the slice comes first
+    // The longest row of the slice (the first one unless rows are grouped: then a slice that straddles two
+    // groups need not start with its longest row).
+    int w = 0;
+    for (int l = 0; l < 32; ++l) w = max(w, len_sorted[s * 32 + l]);
     w = (w + 1) & ~1;
     slice_w[s] = w;
     slice_entries[s] = (int64_t)w * 32;
@@ -386,10 +392,9 @@ static inline unsigned nblk(int64_t n, int t = 256)
 // Order rows of a compressed structure by length (descending, stable) and build the sliced ELL.
 template <typename real>
 static sme_status make_sell(sme_op op, Sell &S, int64_t rows, const int32_t *ptr, const int32_t *idx,
-                            const real *val, const int32_t *len_orig, const int32_t *other_iperm_unused,
+                            const real *val, const int32_t *len_orig, const uint32_t *group, int group_bits,
                             cudaStream_t s)
 {
-    (void)other_iperm_unused;
     S.rows = rows;
     S.nslices = (rows + 31) / 32;
     SME_TRY(dev_alloc(op, (void **)&S.perm, rows * sizeof(int32_t)));
@@ -413,9 +418,13 @@ static sme_status make_sell(sme_op op, Sell &S, int64_t rows, const int32_t *ptr
     SME_CUDA(cudaMallocAsync((void **)&k0, rows * sizeof(uint32_t), s));
     SME_CUDA(cudaMallocAsync((void **)&k1, rows * sizeof(uint32_t), s));
     SME_CUDA(cudaMallocAsync((void **)&v1, rows * sizeof(int32_t), s));
-    length_keys<<<nblk(rows), 256, 0, s>>>(len_orig, rows, maxlen, k0, S.perm);
+    // Rows in descending length (stable), group-major when groups are given and the key fits 32 bits.
+    const int len_bits = std::max(1, bit_length((uint64_t)maxlen));
+    if (group && len_bits + group_bits > 32) group = nullptr;
+    length_keys<<<nblk(rows), 256, 0, s>>>(len_orig, rows, maxlen, group, len_bits, k0, S.perm);
     bool alt = false;
-    SME_TRY(radix_sort_pairs(k0, S.perm, k1, v1, rows, bit_length((uint64_t)maxlen), s, &alt));
+    SME_TRY(radix_sort_pairs(k0, S.perm, k1, v1, rows, group ? len_bits + group_bits : bit_length((uint64_t)maxlen),
+                             s, &alt));
     if (alt) SME_CUDA(cudaMemcpyAsync(S.perm, v1, rows * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     SME_CUDA(cudaFreeAsync(k0, s));
     SME_CUDA(cudaFreeAsync(k1, s));
@@ -454,7 +463,7 @@ static sme_status fill(sme_op op, Sell &S, const int32_t *ptr, const int32_t *id
 
 template <typename real>
 static sme_status build_sparse_t(sme_op op, const int32_t *rp, const int32_t *col, const real *val,
-                                 cudaStream_t s)
+                                 const uint32_t *row_group, const uint32_t *col_group, int group_bits, cudaStream_t s)
 {
     const int64_t m = op->m, n = op->n, nnz = op->nnz;
     SME_CUDA(cudaMemsetAsync(op->d_status, 0, sizeof(int), s));
@@ -499,8 +508,8 @@ static sme_status build_sparse_t(sme_op op, const int32_t *rp, const int32_t *co
     SME_CUDA(cudaGetLastError());
 
     // Length orderings of rows and columns, then the two sliced-ELL copies with renumbered indices.
-    SME_TRY(make_sell<real>(op, op->fwd, m, rp, col, val, row_len, nullptr, s));
-    SME_TRY(make_sell<real>(op, op->bwd, n, col_ptr, t_idx, t_val, col_len, nullptr, s));
+    SME_TRY(make_sell<real>(op, op->fwd, m, rp, col, val, row_len, row_group, group_bits, s));
+    SME_TRY(make_sell<real>(op, op->bwd, n, col_ptr, t_idx, t_val, col_len, col_group, group_bits, s));
     SME_TRY(fill<real>(op, op->fwd, rp, col, val, op->bwd.iperm, s));
     SME_TRY(fill<real>(op, op->bwd, col_ptr, t_idx, t_val, op->fwd.iperm, s));
 
@@ -511,10 +520,12 @@ static sme_status build_sparse_t(sme_op op, const int32_t *rp, const int32_t *co
     return SME_OK;
 }
 
-sme_status build_sparse(sme_op op, const int32_t *rp, const int32_t *col, const void *vals, cudaStream_t s)
+sme_status build_sparse(sme_op op, const int32_t *rp, const int32_t *col, const void *vals, cudaStream_t s,
+                        const uint32_t *row_group, const uint32_t *col_group, int group_bits)
 {
-    if (op->dtype == SME_F64) return build_sparse_t<double>(op, rp, col, (const double *)vals, s);
-    return build_sparse_t<float>(op, rp, col, (const float *)vals, s);
+    if (op->dtype == SME_F64)
+        return build_sparse_t<double>(op, rp, col, (const double *)vals, row_group, col_group, group_bits, s);
+    return build_sparse_t<float>(op, rp, col, (const float *)vals, row_group, col_group, group_bits, s);
 }
 
 }  // namespace sme

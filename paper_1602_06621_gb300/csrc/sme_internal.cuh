@@ -171,8 +171,15 @@ sme_status scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, cudaSt
 sme_status scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);  // out[n] = total
 sme_status radix_sort_pairs(uint32_t *keys, int32_t *vals, uint32_t *keys_alt, int32_t *vals_alt, int64_t n,
                             int key_bits, cudaStream_t s, bool *result_in_alt);
+// Builds both sliced-ELL copies.  row_group / col_group (device, optional, one id per original row / column,
+// ids < 2^group_bits): rows are ordered group-major (ascending id), then by descending length.
 sme_status build_sparse(sme_op op, const int32_t *d_row_ptr, const int32_t *d_col, const void *d_vals,
-                        cudaStream_t s);
+                        cudaStream_t s, const uint32_t *row_group = nullptr, const uint32_t *col_group = nullptr,
+                        int group_bits = 0);
+// sme_op_create_csr with optional host group ids (see build_sparse); used for batches.
+sme_status create_csr_grouped(sme_op *out, int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr,
+                              const int32_t *col_idx, const void *vals, sme_dtype dtype, int on_device, void *stream,
+                              const uint32_t *row_group_host, const uint32_t *col_group_host, int group_bits);
 
 // Equilibration / estimation launches (equilibrate.cu).
 sme_status ensure_equil_workspace(sme_op op, int kw);

@@ -24,9 +24,12 @@ def _batch_run(b, mats, td, **kw):
     return [x.cpu().double().numpy() for x in (u, v, ub, vb)]
 
 
-@pytest.mark.parametrize("k", [16, 32])
-def test_batch_equals_separate_runs_bitwise(k):
+@pytest.mark.parametrize("k,group_bytes", [(16, None), (32, None), (16, 40000)])
+def test_batch_equals_separate_runs_bitwise(k, group_bytes, monkeypatch):
+    """Also with matrices laid out in several L2-sized groups (a small group budget forces several)."""
     import torch
+    if group_bytes:
+        monkeypatch.setenv("SME_BATCH_GROUP_BYTES", str(group_bytes))
     mats = I.batched_family(7, 60, 3000, seed=k)
     b = sme.sme_batch_create(mats)
     try:
@@ -125,12 +128,15 @@ def test_autotuned_shape_gives_identical_results():
         np.testing.assert_array_equal(a, b_)
 
 
-def test_batch_lsqr_matches_per_matrix_lsqr():
+@pytest.mark.parametrize("group_bytes", [None, 20000])
+def test_batch_lsqr_matches_per_matrix_lsqr(group_bytes, monkeypatch):
     """Each matrix of the batch gets its own LSQR.  Against sme_lsqr on the matrix alone (same scalings,
     same right-hand side): the first iterates agree to rounding; converged solves agree in iteration count
     within 2 % (the norms are summed in a different order, and LSQR amplifies rounding over hundreds of
     iterations); every residual is re-checked by the oracle."""
     import torch
+    if group_bytes:
+        monkeypatch.setenv("SME_BATCH_GROUP_BYTES", str(group_bytes))
     mats = I.batched_family(5, 80, 1500, seed=21, dtype=np.float64)
     b = sme.sme_batch_create(mats)
     try:
