@@ -410,13 +410,19 @@ def run_batched(args, rank, world, local):
     # Per-matrix quality and the per-matrix LSQR solve on the last step's scalings (outside the timed region).
     ev = sme.sme_batch_evaluate(b, z[2], z[3])
     spreads = np.array([max(e["row_spread"], e["col_spread"]) for e in ev])
-    x = torch.zeros(N, device="cuda")
-    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0.record(stream)
-    lr = sme.sme_batch_lsqr(b, z[2], z[3], bvec, x, tol=1e-6, max_iters=20000, check_every=10)
-    l1.record(stream)
-    l1.synchronize()
-    its = np.array([r["iters"] for r in lr])
+    lsqr = None
+    if not args.no_lsqr:
+        x = torch.zeros(N, device="cuda")
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        lr = sme.sme_batch_lsqr(b, z[2], z[3], bvec, x, tol=1e-6, max_iters=20000, check_every=10)
+        l1.record(stream)
+        l1.synchronize()
+        its = np.array([r["iters"] for r in lr])
+        lsqr = {"ms": l0.elapsed_time(l1), "converged": int(sum(r["converged"] for r in lr)), "of": count,
+                "iters_median": float(np.median(its)), "iters_p90": float(np.percentile(its, 90)),
+                "iters_max": int(its.max()), "tol": 1e-6, "iteration_cap": 20000,
+                "kernel_launches": int(lr[0]["kernel_launches"])}
     line = {
         "metric": METRIC, "value": world * count * k * T * args.steps / elapsed, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
@@ -432,10 +438,7 @@ def run_batched(args, rank, world, local):
         "gpu_launches": (T + 4) * args.steps, "clocks": clk.summary(),
         "quality": {"spread_median": float(np.median(spreads)), "spread_max": float(spreads.max()),
                     "rms_median": float(np.median([e["rms"] for e in ev]))},
-        "lsqr": {"ms": l0.elapsed_time(l1), "converged": int(sum(r["converged"] for r in lr)), "of": count,
-                 "iters_median": float(np.median(its)), "iters_p90": float(np.percentile(its, 90)),
-                 "iters_max": int(its.max()), "tol": 1e-6, "iteration_cap": 20000,
-                 "kernel_launches": int(lr[0]["kernel_launches"])},
+        "lsqr": lsqr,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
