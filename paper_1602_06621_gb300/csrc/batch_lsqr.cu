@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <memory>
 #include <vector>
 
 #include "sell_ops.cuh"
@@ -268,12 +269,11 @@ static sme_status batch_lsqr_t(sme_op op, const real *ubar, const real *vbar, co
     BatchInfo *B = op->batch;
     const int count = B->count;
     const int64_t M = op->m, N = op->n;
-    BLsqr *L = new BLsqr();
+    // Released on every return path (the early returns of SME_CUDA included).
+    std::unique_ptr<BLsqr, void (*)(BLsqr *)> owner(new BLsqr(), bl_release);
+    BLsqr *L = owner.get();
     L->count = count;
-    auto fail = [&](sme_status e) {
-        bl_release(L);
-        return e;
-    };
+    auto fail = [](sme_status e) { return e; };
     const size_t sz = sizeof(real);
     void **bufs[8] = {&L->ud, &L->bs, &L->d, &L->ve, &L->w, &L->x, &L->e, &L->xt};
     const int64_t lens[8] = {M, M, M, N, N, N, N, N};
@@ -357,7 +357,6 @@ static sme_status batch_lsqr_t(sme_op op, const real *ubar, const real *vbar, co
         all_conv = all_conv && res[b].converged;
         finite = finite && std::isfinite(h.rel_res);
     }
-    bl_release(L);
     if (!finite) {
         set_error("sme_batch_lsqr: a residual became non-finite");
         return SME_ERR_NONFINITE;

@@ -112,13 +112,13 @@ static sme_status scan_exclusive(const T *in, T *out, int64_t n, cudaStream_t s)
         return SME_OK;
     }
     const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
-    T *sums = nullptr;
-    SME_CUDA(cudaMallocAsync((void **)&sums, (ntiles + 1) * sizeof(T), s));
+    AsyncScratch scratch(s);
+    SME_CUDA(scratch.alloc((ntiles + 1) * sizeof(T)));
+    T *sums = scratch.as<T>();
     scan_tile_sums<T><<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(in, n, sums);
     scan_sums_single<T><<<1, SCAN_THREADS, 0, s>>>(sums, ntiles);
     scan_apply<T><<<(unsigned)ntiles, SCAN_THREADS, 0, s>>>(in, n, sums, out, ntiles);
     SME_CUDA(cudaGetLastError());
-    SME_CUDA(cudaFreeAsync(sums, s));
     return SME_OK;
 }
 
@@ -199,8 +199,9 @@ sme_status radix_sort_pairs(uint32_t *keys, int32_t *vals, uint32_t *keys_alt, i
     *result_in_alt = false;
     if (n <= 1 || key_bits <= 0) return SME_OK;
     const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
-    int32_t *hist = nullptr;
-    SME_CUDA(cudaMallocAsync((void **)&hist, (256 * ntiles + 1) * sizeof(int32_t), s));
+    AsyncScratch scratch(s);
+    SME_CUDA(scratch.alloc((256 * ntiles + 1) * sizeof(int32_t)));
+    int32_t *hist = scratch.as<int32_t>();
     uint32_t *ki = keys, *ko = keys_alt;
     int32_t *vi = vals, *vo = vals_alt;
     for (int shift = 0; shift < key_bits; shift += 8) {
@@ -212,7 +213,6 @@ sme_status radix_sort_pairs(uint32_t *keys, int32_t *vals, uint32_t *keys_alt, i
         std::swap(vi, vo);
         *result_in_alt = !*result_in_alt;
     }
-    SME_CUDA(cudaFreeAsync(hist, s));
     return SME_OK;
 }
 
@@ -404,20 +404,20 @@ static sme_status make_sell(sme_op op, Sell &S, int64_t rows, const int32_t *ptr
     SME_TRY(dev_alloc(op, (void **)&S.slice_off, (S.nslices + 1) * sizeof(int64_t)));
     SME_CUDA(cudaMemsetAsync(S.len, 0, S.nslices * 32 * sizeof(int32_t), s));
 
-    int *d_max = nullptr;
-    SME_CUDA(cudaMallocAsync((void **)&d_max, sizeof(int), s));
+    AsyncScratch s_max(s), s_k0(s), s_k1(s), s_v1(s), s_sl(s);
+    SME_CUDA(s_max.alloc(sizeof(int)));
+    int *d_max = s_max.as<int>();
     SME_CUDA(cudaMemsetAsync(d_max, 0, sizeof(int), s));
     max_i32<<<152 * 4, 256, 0, s>>>(len_orig, rows, d_max);
     int maxlen = 0;
     SME_CUDA(cudaMemcpyAsync(&maxlen, d_max, sizeof(int), cudaMemcpyDeviceToHost, s));
     SME_CUDA(cudaStreamSynchronize(s));
-    SME_CUDA(cudaFreeAsync(d_max, s));
 
-    uint32_t *k0 = nullptr, *k1 = nullptr;
-    int32_t *v1 = nullptr;
-    SME_CUDA(cudaMallocAsync((void **)&k0, rows * sizeof(uint32_t), s));
-    SME_CUDA(cudaMallocAsync((void **)&k1, rows * sizeof(uint32_t), s));
-    SME_CUDA(cudaMallocAsync((void **)&v1, rows * sizeof(int32_t), s));
+    SME_CUDA(s_k0.alloc(rows * sizeof(uint32_t)));
+    SME_CUDA(s_k1.alloc(rows * sizeof(uint32_t)));
+    SME_CUDA(s_v1.alloc(rows * sizeof(int32_t)));
+    uint32_t *k0 = s_k0.as<uint32_t>(), *k1 = s_k1.as<uint32_t>();
+    int32_t *v1 = s_v1.as<int32_t>();
     // Rows in descending length (stable), group-major when groups are given and the key fits 32 bits.
     const int len_bits = std::max(1, bit_length((uint64_t)maxlen));
     if (group && len_bits + group_bits > 32) group = nullptr;
@@ -426,16 +426,12 @@ static sme_status make_sell(sme_op op, Sell &S, int64_t rows, const int32_t *ptr
     SME_TRY(radix_sort_pairs(k0, S.perm, k1, v1, rows, group ? len_bits + group_bits : bit_length((uint64_t)maxlen),
                              s, &alt));
     if (alt) SME_CUDA(cudaMemcpyAsync(S.perm, v1, rows * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    SME_CUDA(cudaFreeAsync(k0, s));
-    SME_CUDA(cudaFreeAsync(k1, s));
-    SME_CUDA(cudaFreeAsync(v1, s));
     invert_perm<<<nblk(rows), 256, 0, s>>>(S.perm, rows, S.iperm, len_orig, S.len);
 
-    int64_t *sl_entries = nullptr;
-    SME_CUDA(cudaMallocAsync((void **)&sl_entries, S.nslices * sizeof(int64_t), s));
+    SME_CUDA(s_sl.alloc(S.nslices * sizeof(int64_t)));
+    int64_t *sl_entries = s_sl.as<int64_t>();
     slice_sizes<<<nblk(S.nslices), 256, 0, s>>>(S.len, rows, S.nslices, S.slice_w, sl_entries);
     SME_TRY(scan_exclusive_i64(sl_entries, S.slice_off, S.nslices, s));
-    SME_CUDA(cudaFreeAsync(sl_entries, s));
     SME_CUDA(cudaMemcpyAsync(&S.entries, S.slice_off + S.nslices, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     SME_CUDA(cudaStreamSynchronize(s));
     (void)ptr;
@@ -481,21 +477,24 @@ static sme_status build_sparse_t(sme_op op, const int32_t *rp, const int32_t *co
     }
 
     // Transposed copy: stable sort of the nonzeros by column.
-    int32_t *row_len = nullptr, *row_of = nullptr, *col_len = nullptr, *col_ptr = nullptr, *t_idx = nullptr;
-    real *t_val = nullptr;
-    uint32_t *k0 = nullptr, *k1 = nullptr;
-    int32_t *e0 = nullptr, *e1 = nullptr;
     const int64_t nz1 = std::max<int64_t>(nnz, 1);
-    SME_CUDA(cudaMallocAsync((void **)&row_len, m * sizeof(int32_t), s));
-    SME_CUDA(cudaMallocAsync((void **)&row_of, nz1 * sizeof(int32_t), s));
-    SME_CUDA(cudaMallocAsync((void **)&col_len, n * sizeof(int32_t), s));
-    SME_CUDA(cudaMallocAsync((void **)&col_ptr, (n + 1) * sizeof(int32_t), s));
-    SME_CUDA(cudaMallocAsync((void **)&t_idx, nz1 * sizeof(int32_t), s));
-    SME_CUDA(cudaMallocAsync((void **)&t_val, nz1 * sizeof(real), s));
-    SME_CUDA(cudaMallocAsync((void **)&k0, nz1 * sizeof(uint32_t), s));
-    SME_CUDA(cudaMallocAsync((void **)&k1, nz1 * sizeof(uint32_t), s));
-    SME_CUDA(cudaMallocAsync((void **)&e0, nz1 * sizeof(int32_t), s));
-    SME_CUDA(cudaMallocAsync((void **)&e1, nz1 * sizeof(int32_t), s));
+    AsyncScratch g_row_len(s), g_row_of(s), g_col_len(s), g_col_ptr(s), g_t_idx(s), g_t_val(s), g_k0(s), g_k1(s),
+        g_e0(s), g_e1(s);
+    SME_CUDA(g_row_len.alloc(m * sizeof(int32_t)));
+    SME_CUDA(g_row_of.alloc(nz1 * sizeof(int32_t)));
+    SME_CUDA(g_col_len.alloc(n * sizeof(int32_t)));
+    SME_CUDA(g_col_ptr.alloc((n + 1) * sizeof(int32_t)));
+    SME_CUDA(g_t_idx.alloc(nz1 * sizeof(int32_t)));
+    SME_CUDA(g_t_val.alloc(nz1 * sizeof(real)));
+    SME_CUDA(g_k0.alloc(nz1 * sizeof(uint32_t)));
+    SME_CUDA(g_k1.alloc(nz1 * sizeof(uint32_t)));
+    SME_CUDA(g_e0.alloc(nz1 * sizeof(int32_t)));
+    SME_CUDA(g_e1.alloc(nz1 * sizeof(int32_t)));
+    int32_t *row_len = g_row_len.as<int32_t>(), *row_of = g_row_of.as<int32_t>(), *col_len = g_col_len.as<int32_t>(),
+            *col_ptr = g_col_ptr.as<int32_t>(), *t_idx = g_t_idx.as<int32_t>();
+    real *t_val = g_t_val.as<real>();
+    uint32_t *k0 = g_k0.as<uint32_t>(), *k1 = g_k1.as<uint32_t>();
+    int32_t *e0 = g_e0.as<int32_t>(), *e1 = g_e1.as<int32_t>();
     row_lengths<<<nblk(m), 256, 0, s>>>(rp, m, row_len, row_of);
     if (nnz > 0) iota_u32<<<nblk(nnz), 256, 0, s>>>(k0, col, e0, nnz);
     bool alt = false;
@@ -513,9 +512,6 @@ static sme_status build_sparse_t(sme_op op, const int32_t *rp, const int32_t *co
     SME_TRY(fill<real>(op, op->fwd, rp, col, val, op->bwd.iperm, s));
     SME_TRY(fill<real>(op, op->bwd, col_ptr, t_idx, t_val, op->fwd.iperm, s));
 
-    for (void *p : {(void *)row_len, (void *)row_of, (void *)col_len, (void *)col_ptr, (void *)t_idx,
-                    (void *)t_val, (void *)k0, (void *)k1, (void *)e0, (void *)e1})
-        SME_CUDA(cudaFreeAsync(p, s));
     SME_CUDA(cudaStreamSynchronize(s));
     return SME_OK;
 }

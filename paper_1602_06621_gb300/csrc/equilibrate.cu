@@ -750,9 +750,10 @@ static sme_status block_t(sme_op op, const sme_equil_params *p, int64_t pb, cons
     for (int64_t c = 0; c < qb; ++c)
         for (int64_t j = cb_h[c]; j < cb_h[c + 1]; ++j) bc[j] = (int32_t)c;
     const size_t sz = sizeof(real);
-    char *buf = nullptr;
     const size_t bytes = (size_t)(m + n) * 4 + (size_t)(pb + qb + 2) * 8 + (size_t)2 * (m + n) * sz;
-    SME_CUDA(cudaMallocAsync((void **)&buf, bytes, s));
+    AsyncScratch scratch(s);
+    SME_CUDA(scratch.alloc(bytes));
+    char *buf = scratch.as<char>();
     int32_t *dbr = (int32_t *)buf, *dbc = dbr + m;
     int64_t *drb = (int64_t *)(buf + (size_t)(m + n) * 4), *dcb = drb + pb + 1;
     real *xr = (real *)(buf + (size_t)(m + n) * 4 + (size_t)(pb + qb + 2) * 8), *xc = xr + m, *zu = xc + n,
@@ -772,7 +773,6 @@ static sme_status block_t(sme_op op, const sme_equil_params *p, int64_t pb, cons
                                                                    (double)t / ((double)t + 2.0), op->d_status);
     }
     SME_CUDA(cudaGetLastError());
-    SME_CUDA(cudaFreeAsync(buf, s));
     return SME_OK;
 }
 
@@ -787,9 +787,9 @@ static sme_status autotune_t(sme_op op, int k, cudaStream_t s, int *spc_out, int
                       0, s);
     launch_load<real>(op, 1, kw, (const real *)nullptr, nullptr, (real *)op->ws.v, nullptr, op->ws.tab_v[0], 1u, 0u,
                       0, s);
-    cudaEvent_t e0, e1;
-    SME_CUDA(cudaEventCreate(&e0));
-    SME_CUDA(cudaEventCreate(&e1));
+    EventPair ev;
+    SME_CUDA(ev.create());
+    cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
     const int spcs[3] = {4, 8, 16};
     float best = 1e30f;
     Shape best_sh;
@@ -816,8 +816,6 @@ static sme_status autotune_t(sme_op op, int k, cudaStream_t s, int *spc_out, int
                 best_sh = sh;
             }
         }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     const int slot = k_slot(k);
     if (slot < 8) {
         op->tuned[slot].spc = best_sh.spc;

@@ -159,9 +159,10 @@ static sme_status evaluate_t(sme_op op, const real *u, const real *v, double alp
                              double *r2_out, double *c2_out, sme_eval_result *res, cudaStream_t s)
 {
     const int64_t m = op->m, n = op->n;
-    double *buf = nullptr;
     const int NB = 152;
-    SME_CUDA(cudaMallocAsync((void **)&buf, (size_t)(2 * (m + n)) * sizeof(double) + 2 * NB * sizeof(EvalPart), s));
+    AsyncScratch scratch(s);
+    SME_CUDA(scratch.alloc((size_t)(2 * (m + n)) * sizeof(double) + 2 * NB * sizeof(EvalPart)));
+    double *buf = scratch.as<double>();
     double *sq_u = buf, *sq_v = buf + m, *r2 = buf + m + n, *c2 = buf + 2 * m + n;
     EvalPart *parts = (EvalPart *)(buf + 2 * (m + n));
     if (r2_out) r2 = r2_out;
@@ -174,9 +175,7 @@ static sme_status evaluate_t(sme_op op, const real *u, const real *v, double alp
         exact_norms_kernel<real><<<nblk(op->fwd.nslices * 32), 256, 0, s>>>(op->fwd, op->dbl, sq_v, u, r2);
         exact_norms_kernel<real><<<nblk(op->bwd.nslices * 32), 256, 0, s>>>(op->bwd, op->dbl, sq_u, v, c2);
     }
-    const sme_status st = evaluate_from_norms<real>(m, n, r2, c2, u, v, alpha, beta, gamma, res, parts, s);
-    cudaFreeAsync(buf, s);
-    return st;
+    return evaluate_from_norms<real>(m, n, r2, c2, u, v, alpha, beta, gamma, res, parts, s);
 }
 
 // Per-matrix partials of a batch: block (b, side) reduces matrix b's rows (side 0) or columns (side 1), whose
@@ -245,9 +244,10 @@ static sme_status batch_evaluate_t(sme_op op, const real *u, const real *v, doub
         targets[b] = al[b];
         targets[count + b] = be[b];
     }
-    char *buf = nullptr;
     const size_t bytes = (size_t)(2 * (m + n)) * 8 + offs.size() * 8 + targets.size() * 8 + 2 * count * sizeof(EvalPart);
-    SME_CUDA(cudaMallocAsync((void **)&buf, bytes, s));
+    AsyncScratch scratch(s);
+    SME_CUDA(scratch.alloc(bytes));
+    char *buf = scratch.as<char>();
     double *sq_u = (double *)buf, *sq_v = sq_u + m, *r2 = sq_v + n, *c2 = r2 + m;
     int64_t *d_off = (int64_t *)(c2 + n);
     double *d_tg = (double *)(d_off + offs.size());
@@ -264,7 +264,6 @@ static sme_status batch_evaluate_t(sme_op op, const real *u, const real *v, doub
     std::vector<EvalPart> h(2 * count);
     SME_CUDA(cudaMemcpyAsync(h.data(), parts, h.size() * sizeof(EvalPart), cudaMemcpyDeviceToHost, s));
     SME_CUDA(cudaStreamSynchronize(s));
-    SME_CUDA(cudaFreeAsync(buf, s));
     for (int b = 0; b < count; ++b) {
         const EvalPart &R = h[b], &C = h[count + b];
         sme_eval_result &o = res[b];

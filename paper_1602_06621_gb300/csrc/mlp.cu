@@ -372,9 +372,10 @@ static sme_status features_t(sme_op op, uint64_t seed, float *rowF, float *colF,
     } else {
         offs = {0, m, 0, n};
     }
-    char *buf = nullptr;
     const size_t bytes = (size_t)(m + n) * (sizeof(real) * 2 + 8) + offs.size() * 8 + 2 * (size_t)count * 4 + 64;
-    SME_CUDA(cudaMallocAsync((void **)&buf, bytes, s));
+    AsyncScratch scratch(s);
+    SME_CUDA(scratch.alloc(bytes));
+    char *buf = scratch.as<char>();
     real *u0 = (real *)buf, *v0 = u0 + m, *zu = v0 + n, *zv = zu + m;
     float *cnt = (float *)(zv + n), *mab = cnt + (m + n);
     int64_t *d_off = (int64_t *)(((uintptr_t)(mab + (m + n)) + 15) & ~(uintptr_t)15);
@@ -394,7 +395,6 @@ static sme_status features_t(sme_op op, uint64_t seed, float *rowF, float *colF,
         assemble_features<real><<<nblk(n), 256, 0, s>>>(n, zv, cnt + m, mab + m, 1.f, count, off_c, off_r, off_c, mu,
                                                         mu + count, colF);
     SME_CUDA(cudaGetLastError());
-    SME_CUDA(cudaFreeAsync(buf, s));
     return SME_OK;
 }
 
@@ -570,8 +570,9 @@ extern "C" sme_status sme_warm_start(sme_op op, sme_mlp M, uint64_t seed, void *
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t m = op->m, n = op->n;
-    float *buf = nullptr;
-    SME_CUDA(cudaMallocAsync((void **)&buf, (size_t)(m + n) * (MLP_IN + 1) * sizeof(float), s));
+    AsyncScratch scratch(s);
+    SME_CUDA(scratch.alloc((size_t)(m + n) * (MLP_IN + 1) * sizeof(float)));
+    float *buf = scratch.as<float>();
     float *F = buf, *y = buf + (m + n) * MLP_IN;
     SME_TRY(sme_op_features(op, seed, F, F + m * MLP_IN, stream));
     SME_TRY(sme_mlp_forward(M, F, m + n, y, stream));
@@ -583,7 +584,6 @@ extern "C" sme_status sme_warm_start(sme_op op, sme_mlp M, uint64_t seed, void *
         cast_out<float><<<nblk(n), 256, 0, s>>>(n, y + m, (float *)v0);
     }
     SME_CUDA(cudaGetLastError());
-    SME_CUDA(cudaFreeAsync(buf, s));
     return SME_OK;
 }
 

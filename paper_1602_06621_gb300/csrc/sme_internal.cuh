@@ -29,6 +29,38 @@ sme_status cuda_fail(cudaError_t e, const char *what, int line);
         if (_s != SME_OK) return _s;         \
     } while (0)
 
+// Stream-ordered scratch that is released when its scope ends, on every return path (including the early
+// returns of SME_CUDA / SME_TRY).
+struct AsyncScratch {
+    void *p = nullptr;
+    cudaStream_t s = nullptr;
+    explicit AsyncScratch(cudaStream_t st) : s(st) {}
+    ~AsyncScratch()
+    {
+        if (p) cudaFreeAsync(p, s);
+    }
+    AsyncScratch(const AsyncScratch &) = delete;
+    AsyncScratch &operator=(const AsyncScratch &) = delete;
+    cudaError_t alloc(size_t bytes) { return cudaMallocAsync(&p, bytes, s); }
+    template <typename T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+// A pair of timing events destroyed with their scope.
+struct EventPair {
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    ~EventPair()
+    {
+        for (cudaEvent_t x : e)
+            if (x) cudaEventDestroy(x);
+    }
+    cudaError_t create()
+    {
+        cudaError_t r = cudaEventCreate(&e[0]);
+        return r == cudaSuccess ? cudaEventCreate(&e[1]) : r;
+    }
+};
+
 // Device status word bits (set by kernels, read by sme_op_check).
 enum : int {
     ST_NONFINITE = 1,
