@@ -60,37 +60,32 @@ __global__ void ccp_power_init(int64_t n, const real *e, real *xe, CcpScalars *s
 }
 
 // Power iteration, rows: yd = D (K p) with K p = D A (E p); p is xe * inv_lam_pw.
-template <typename real>
+template <typename real, int SPLIT>
 __global__ void __launch_bounds__(LQ_THREADS) ccp_power_rows(Sell S, const real *d, const real *xe, real *yd,
                                                               const CcpScalars *sc)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
-    if (slice >= S.nslices) return;
-    const real acc = sell_row_dot<real, real, real>(S, slice, lane, xe);
-    const int64_t r = slice * 32 + lane;
-    if (r >= S.rows) return;
+    const SplitSlice<SPLIT> w;
+    const real acc = sell_row_dot_split<real, real, real, SPLIT>(S, w, xe);
+    const int64_t r = w.slice * 32 + w.lane;
+    if (!w.lead() || w.slice >= S.nslices || r >= S.rows) return;
     const real dr = d[r];
     yd[r] = dr * dr * acc * (real)sc->inv_lam_pw;
 }
 
 // Power iteration, columns: q = K^T (K p) = E A^T (D K p); xe = E q; ||q|| reduced in FP64.
-template <typename real>
+template <typename real, int SPLIT>
 __global__ void __launch_bounds__(LQ_THREADS) ccp_power_cols(Sell S, const real *e, const real *yd, real *xe,
                                                               double *partials, unsigned *counter, CcpScalars *sc)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
+    const SplitSlice<SPLIT> w;
+    const real acc = sell_row_dot_split<real, real, real, SPLIT>(S, w, yd);
+    const int64_t c = w.slice * 32 + w.lane;
     double part = 0.0;
-    if (slice < S.nslices) {
-        const real acc = sell_row_dot<real, real, real>(S, slice, lane, yd);
-        const int64_t c = slice * 32 + lane;
-        if (c < S.rows) {
-            const real ec = e[c];
-            const real q = ec * acc;
-            xe[c] = ec * q;
-            part = (double)q * (double)q;
-        }
+    if (w.lead() && w.slice < S.nslices && c < S.rows) {
+        const real ec = e[c];
+        const real q = ec * acc;
+        xe[c] = ec * q;
+        part = (double)q * (double)q;
     }
     if (!arrive_last(part, partials, counter)) return;
     const double tot = sum_partials(partials, counter);
@@ -136,51 +131,46 @@ __global__ void ccp_init_cols(int64_t n, real *xs, real *xe)
 }
 
 // Dual step (rows): w = y + sigma d (A xe), y <- a (w - sigma d b) / (a + sigma), yd = d y.
-template <typename real>
+template <typename real, int SPLIT>
 __global__ void __launch_bounds__(LQ_THREADS) ccp_rows(Sell S, const real *d, const real *bs, const real *xe,
                                                         real *y, real *yd, const CcpScalars *sc)
 {
-    if (((volatile const CcpScalars *)sc)->done) return;
+    if (((volatile const CcpScalars *)sc)->done) return;  // the same for every thread of the block
     const real sigma = (real)sc->sigma;
     const double sqrt_lam = sc->sqrt_lam;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
-    if (slice >= S.nslices) return;
-    const real acc = sell_row_dot<real, real, real>(S, slice, lane, xe);
-    const int64_t r = slice * 32 + lane;
-    if (r >= S.rows) return;
+    const SplitSlice<SPLIT> w;
+    const real acc = sell_row_dot_split<real, real, real, SPLIT>(S, w, xe);
+    const int64_t r = w.slice * 32 + w.lane;
+    if (!w.lead() || w.slice >= S.nslices || r >= S.rows) return;
     const real dr = d[r];
-    const real w = y[r] + sigma * dr * acc;
+    const real wv = y[r] + sigma * dr * acc;
     const real a = (real)(2.0 / ((double)dr * (double)dr * sqrt_lam));
-    const real yn = a * (w - sigma * dr * bs[r]) / (a + sigma);
+    const real yn = a * (wv - sigma * dr * bs[r]) / (a + sigma);
     y[r] = yn;
     yd[r] = dr * yn;
 }
 
 // Primal step (columns): xs' = soft(xs - tau e (A^T yd), tau sqrt(lam) e), xbar = xs' + theta (xs' - xs),
 // xe = e xbar.  The last block counts the iteration.
-template <typename real>
+template <typename real, int SPLIT>
 __global__ void __launch_bounds__(LQ_THREADS) ccp_cols(Sell S, const real *e, const real *yd, real *xs, real *xe,
                                                         unsigned *counter, CcpScalars *sc)
 {
-    if (((volatile const CcpScalars *)sc)->done) return;
+    if (((volatile const CcpScalars *)sc)->done) return;  // the same for every thread of the block
     const real tau = (real)sc->tau, theta = (real)sc->theta;
     const real thr0 = (real)(sc->tau * sc->sqrt_lam);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
-    if (slice < S.nslices) {
-        const real acc = sell_row_dot<real, real, real>(S, slice, lane, yd);
-        const int64_t c = slice * 32 + lane;
-        if (c < S.rows) {
-            const real ec = e[c];
-            const real xo = xs[c];
-            const real z = xo - tau * ec * acc;
-            const real thr = thr0 * ec;
-            const real az = z < real(0) ? -z : z;
-            const real xn = az > thr ? (z < real(0) ? -(az - thr) : az - thr) : real(0);
-            xs[c] = xn;
-            xe[c] = ec * (xn + theta * (xn - xo));
-        }
+    const SplitSlice<SPLIT> w;
+    const real acc = sell_row_dot_split<real, real, real, SPLIT>(S, w, yd);
+    const int64_t c = w.slice * 32 + w.lane;
+    if (w.lead() && w.slice < S.nslices && c < S.rows) {
+        const real ec = e[c];
+        const real xo = xs[c];
+        const real z = xo - tau * ec * acc;
+        const real thr = thr0 * ec;
+        const real az = z < real(0) ? -z : z;
+        const real xn = az > thr ? (z < real(0) ? -(az - thr) : az - thr) : real(0);
+        xs[c] = xn;
+        xe[c] = ec * (xn + theta * (xn - xo));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -212,21 +202,18 @@ __global__ void ccp_current_x(int64_t n, const real *e, const real *xs, real *xt
 }
 
 // f(x) = ||A x - b||^2 / sqrt(lam) + sqrt(lam) ||x||_1 in FP64 on the original system; the stopping rule.
-template <typename real>
+template <typename real, int SPLIT>
 __global__ void __launch_bounds__(LQ_THREADS) ccp_objective(Sell S, const real *xt, const real *bs, double *partials,
                                                              unsigned *counter, CcpScalars *sc, int final_pass)
 {
-    if (!final_pass && ((volatile const CcpScalars *)sc)->done) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
+    if (!final_pass && ((volatile const CcpScalars *)sc)->done) return;  // uniform over the block
+    const SplitSlice<SPLIT> w;
+    const double acc = sell_row_dot_split<real, double, real, SPLIT>(S, w, xt);
+    const int64_t i = w.slice * 32 + w.lane;
     double part = 0.0;
-    if (slice < S.nslices) {
-        const double acc = sell_row_dot<real, double, real>(S, slice, lane, xt);
-        const int64_t i = slice * 32 + lane;
-        if (i < S.rows) {
-            const double ri = acc - (double)bs[i];
-            part = ri * ri;
-        }
+    if (w.lead() && w.slice < S.nslices && i < S.rows) {
+        const double ri = acc - (double)bs[i];
+        part = ri * ri;
     }
     if (!arrive_last(part, partials, counter)) return;
     const double tot = sum_partials(partials, counter);
@@ -238,7 +225,60 @@ __global__ void __launch_bounds__(LQ_THREADS) ccp_objective(Sell S, const real *
     }
 }
 
+// Launch geometry of one sliced-ELL pass with SPLIT warps per slice.
+struct Pass {
+    int split;
+    unsigned blocks;
+};
+
+static Pass pass_for(const Sell &S)
+{
+    const int sp = split_for(S);
+    const int64_t per_block = LQ_THREADS / 32 / sp;
+    return Pass{sp, (unsigned)std::max<int64_t>((S.nslices + per_block - 1) / per_block, 1)};
+}
+
+// Dispatch a kernel template over the split factor.
+#define CCP_LAUNCH(kernel, real, pass, s, ...)                                                    \
+    do {                                                                                          \
+        switch ((pass).split) {                                                                   \
+            case 8: kernel<real, 8><<<(pass).blocks, LQ_THREADS, 0, s>>>(__VA_ARGS__); break;     \
+            case 4: kernel<real, 4><<<(pass).blocks, LQ_THREADS, 0, s>>>(__VA_ARGS__); break;     \
+            case 2: kernel<real, 2><<<(pass).blocks, LQ_THREADS, 0, s>>>(__VA_ARGS__); break;     \
+            default: kernel<real, 1><<<(pass).blocks, LQ_THREADS, 0, s>>>(__VA_ARGS__); break;    \
+        }                                                                                         \
+    } while (0)
+
 static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// A CUDA graph captured once from a stream of launches (on its own stream) and destroyed with its scope;
+// exec stays null when capture is not possible, and the caller then launches directly.
+struct GraphOnce {
+    cudaGraphExec_t exec = nullptr;
+    template <typename F>
+    void capture(F &&enqueue)
+    {
+        cudaStream_t q = nullptr;
+        if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            enqueue(q);
+            if (cudaStreamEndCapture(q, &g) == cudaSuccess && g) {
+                if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
+                cudaGraphDestroy(g);
+            }
+        }
+        cudaGetLastError();
+        cudaStreamDestroy(q);
+    }
+    ~GraphOnce()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
 
 static void ccp_release(CcpState *C)
 {
@@ -252,7 +292,8 @@ static void ccp_release(CcpState *C)
 static sme_status ccp_alloc(sme_op op, CcpState *C, size_t sz)
 {
     const int64_t m = op->m, n = op->n;
-    const int64_t maxb = std::max<int64_t>(std::max<int64_t>((op->fwd.nslices + 7) / 8, (op->bwd.nslices + 7) / 8),
+    // One partial per block of any pass: at most one block per slice (8 warps on one slice).
+    const int64_t maxb = std::max<int64_t>(std::max<int64_t>(op->fwd.nslices, op->bwd.nslices),
                                            (std::max(m, n) + 255) / 256);
     void **mv[5] = {&C->d, &C->bs, &C->y, &C->yd, nullptr};
     void **nv[5] = {&C->e, &C->xs, &C->xe, &C->xt, nullptr};
@@ -274,14 +315,12 @@ template <typename real>
 static sme_status power_norm_t(sme_op op, CcpState *C, int iters, double *norm, int64_t *launches, cudaStream_t s)
 {
     const Sell &F = op->fwd, &B = op->bwd;
-    const unsigned fb = (unsigned)std::max<int64_t>((F.nslices + 7) / 8, 1);
-    const unsigned bb = (unsigned)std::max<int64_t>((B.nslices + 7) / 8, 1);
+    const Pass pf = pass_for(F), pb = pass_for(B);
     ccp_power_init<real><<<nblk(op->n), 256, 0, s>>>(op->n, (const real *)C->e, (real *)C->xe, C->sc);
     for (int i = 0; i < iters; ++i) {
-        ccp_power_rows<real><<<fb, LQ_THREADS, 0, s>>>(F, (const real *)C->d, (const real *)C->xe, (real *)C->yd,
-                                                       C->sc);
-        ccp_power_cols<real><<<bb, LQ_THREADS, 0, s>>>(B, (const real *)C->e, (const real *)C->yd, (real *)C->xe,
-                                                       C->partials, C->counter, C->sc);
+        CCP_LAUNCH(ccp_power_rows, real, pf, s, F, (const real *)C->d, (const real *)C->xe, (real *)C->yd, C->sc);
+        CCP_LAUNCH(ccp_power_cols, real, pb, s, B, (const real *)C->e, (const real *)C->yd, (real *)C->xe,
+                   C->partials, C->counter, C->sc);
     }
     *launches += 1 + 2 * (int64_t)iters;
     SME_CUDA(cudaGetLastError());
@@ -340,26 +379,40 @@ static sme_status ccp_t(sme_op op, const real *ubar, const real *vbar, const rea
         return done(SME_ERR_CUDA);
     const Sell &F = op->fwd, &B = op->bwd;
     const int64_t m = op->m, n = op->n;
-    const unsigned fb = (unsigned)std::max<int64_t>((F.nslices + 7) / 8, 1);
-    const unsigned bb = (unsigned)std::max<int64_t>((B.nslices + 7) / 8, 1);
+    const Pass pf = pass_for(F), pb = pass_for(B);
     real *d = (real *)C->d, *e = (real *)C->e, *bs = (real *)C->bs, *y = (real *)C->y, *yd = (real *)C->yd,
          *xs = (real *)C->xs, *xe = (real *)C->xe, *xt = (real *)C->xt;
     ccp_init_rows<real><<<nblk(m), 256, 0, s>>>(m, F.perm, b, bs, y, yd, C->partials, C->counter, C->sc);
     ccp_init_cols<real><<<nblk(n), 256, 0, s>>>(n, xs, xe);
     launches += 2;
     const int every = std::max(1, p->check_every);
+    // A chunk of `every` iterations and its objective check, all on fixed buffers.
+    auto enqueue_chunk = [&](int64_t chunk, cudaStream_t q) {
+        for (int64_t j = 0; j < chunk; ++j) {
+            CCP_LAUNCH(ccp_rows, real, pf, q, F, d, bs, xe, y, yd, C->sc);
+            CCP_LAUNCH(ccp_cols, real, pb, q, B, e, yd, xs, xe, C->counter, C->sc);
+        }
+        ccp_current_x<real><<<nblk(n), 256, 0, q>>>(n, e, xs, xt, nullptr, nullptr, C->partials, C->counter, C->sc,
+                                                   0);
+        CCP_LAUNCH(ccp_objective, real, pf, q, F, xt, bs, C->partials, C->counter, C->sc, 0);
+    };
+    // Full chunks are captured once as a CUDA graph and replayed (on a private stream: the caller's may be
+    // the legacy default stream, which cannot be captured); without a graph they are launched directly.
+    GraphOnce chunk_graph;
+    if (p->max_iters >= 2 * (int64_t)every) chunk_graph.capture([&](cudaStream_t q) { enqueue_chunk(every, q); });
     int64_t it = 0, hcount = 0;
     bool stop = false;
     while (it < p->max_iters && !stop) {
         const int64_t chunk = std::min<int64_t>(every, p->max_iters - it);
-        for (int64_t j = 0; j < chunk; ++j) {
-            ccp_rows<real><<<fb, LQ_THREADS, 0, s>>>(F, d, bs, xe, y, yd, C->sc);
-            ccp_cols<real><<<bb, LQ_THREADS, 0, s>>>(B, e, yd, xs, xe, C->counter, C->sc);
+        if (chunk == every && chunk_graph.exec) {
+            if (cudaGraphLaunch(chunk_graph.exec, s) != cudaSuccess) {
+                cuda_fail(cudaGetLastError(), "sme_ccp_lasso", __LINE__);
+                return done(SME_ERR_CUDA);
+            }
+        } else {
+            enqueue_chunk(chunk, s);
         }
         it += chunk;
-        ccp_current_x<real><<<nblk(n), 256, 0, s>>>(n, e, xs, xt, nullptr, nullptr, C->partials, C->counter, C->sc,
-                                                   0);
-        ccp_objective<real><<<fb, LQ_THREADS, 0, s>>>(F, xt, bs, C->partials, C->counter, C->sc, 0);
         launches += 2 * chunk + 2;
         if (cudaGetLastError() != cudaSuccess ||
             cudaMemcpyAsync(C->host, C->sc, sizeof(CcpScalars), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -376,7 +429,7 @@ static sme_status ccp_t(sme_op op, const real *ubar, const real *vbar, const rea
         stop = C->host->done != 0;
     }
     ccp_current_x<real><<<nblk(n), 256, 0, s>>>(n, e, xs, xt, B.perm, x_out, C->partials, C->counter, C->sc, 1);
-    ccp_objective<real><<<fb, LQ_THREADS, 0, s>>>(F, xt, bs, C->partials, C->counter, C->sc, 1);
+    CCP_LAUNCH(ccp_objective, real, pf, s, F, xt, bs, C->partials, C->counter, C->sc, 1);
     launches += 2;
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(C->host, C->sc, sizeof(CcpScalars), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -82,13 +82,13 @@ __device__ __forceinline__ void pair_load(const Sell &S, int64_t pi, int &c0, re
     }
 }
 
-// sum_l a_l * g[c_l] over the row owned by this thread (acc type `acc_t`), software-pipelined.
+// sum_l a_l * g[c_l] over pair steps [q0, q1) of the row owned by this thread (acc type `acc_t`),
+// software-pipelined: the entries two steps ahead and the gathers one step ahead are in flight.
 template <typename real, typename acc_t, typename G>
-__device__ __forceinline__ acc_t sell_row_dot(const Sell &S, int64_t slice, int lane, const G *g, bool active = true)
+__device__ __forceinline__ acc_t sell_row_dot_range(const Sell &S, int64_t slice, int lane, const G *g, int q0, int q1)
 {
-    // An inactive lane loads nothing and returns 0 (its row belongs to a finished problem).
-    const int np = active ? S.slice_w[slice] / 2 : 0;
-    const int64_t pbase = S.slice_off[slice] / 2 + lane;
+    const int np = q1 - q0;
+    const int64_t pbase = S.slice_off[slice] / 2 + lane + (int64_t)q0 * 32;
     acc_t acc = acc_t(0);
     int c0 = 0, c1 = 0, n0 = 0, n1 = 0;
     real a0 = 0, a1 = 0, b0 = 0, b1 = 0;
@@ -116,6 +116,60 @@ __device__ __forceinline__ acc_t sell_row_dot(const Sell &S, int64_t slice, int 
         g1 = h1;
     }
     return acc;
+}
+
+// The whole row owned by this thread.
+template <typename real, typename acc_t, typename G>
+__device__ __forceinline__ acc_t sell_row_dot(const Sell &S, int64_t slice, int lane, const G *g, bool active = true)
+{
+    // An inactive lane loads nothing and returns 0 (its row belongs to a finished problem).
+    return sell_row_dot_range<real, acc_t, G>(S, slice, lane, g, 0, active ? S.slice_w[slice] / 2 : 0);
+}
+
+// Slices of long rows shared by SPLIT warps of a LQ_THREADS-thread block: warp w takes slice
+// blockIdx.x * (8 / SPLIT) + w / SPLIT and the w % SPLIT-th contiguous range of its pair steps, so loads
+// stay coalesced and a slice's latency chain is SPLIT times shorter.  The partial sums are added in warp
+// order (deterministic) and the full row sum is returned in the slice's first warp (part 0); every thread
+// of the block must call this (it synchronises the block).
+template <int SPLIT>
+struct SplitSlice {
+    int64_t slice;
+    int part, lane;
+    __device__ __forceinline__ SplitSlice()
+    {
+        const int warp = threadIdx.x >> 5;
+        lane = threadIdx.x & 31;
+        slice = (int64_t)blockIdx.x * (LQ_THREADS / 32 / SPLIT) + warp / SPLIT;
+        part = warp % SPLIT;
+    }
+    __device__ __forceinline__ bool lead() const { return part == 0; }
+};
+
+template <typename real, typename acc_t, typename G, int SPLIT>
+__device__ __forceinline__ acc_t sell_row_dot_split(const Sell &S, const SplitSlice<SPLIT> &w, const G *g)
+{
+    acc_t acc = acc_t(0);
+    if (w.slice < S.nslices) {
+        const int np = S.slice_w[w.slice] / 2;
+        acc = sell_row_dot_range<real, acc_t, G>(S, w.slice, w.lane, g, np * w.part / SPLIT,
+                                                 np * (w.part + 1) / SPLIT);
+    }
+    if (SPLIT == 1) return acc;
+    __shared__ acc_t partial[LQ_THREADS];
+    partial[threadIdx.x] = acc;
+    __syncthreads();
+    acc_t tot = acc_t(0);
+    if (w.part == 0)
+        for (int p = 0; p < SPLIT; ++p) tot += partial[threadIdx.x + p * 32];
+    __syncthreads();
+    return tot;
+}
+
+// Warps per slice for a sliced-ELL copy: enough that a lane walks about 16 pair steps or fewer.
+inline int split_for(const Sell &S)
+{
+    const double steps = S.nslices > 0 ? (double)S.entries / (64.0 * (double)S.nslices) : 0.0;
+    return steps >= 96 ? 8 : steps >= 48 ? 4 : steps >= 24 ? 2 : 1;
 }
 
 }  // namespace sme

@@ -43,11 +43,15 @@ def test_operator_norm_matches_oracle_power_iteration(dtype):
     assert plain == pytest.approx(C.power_norm(K0, 60), rel=tol)
 
 
-@pytest.mark.parametrize("dtype", [np.float64, np.float32])
-def test_iterates_and_objective_history_match_oracle(dtype):
-    """Same iteration on both sides (same steps, same order): x after 60 iterations and f(x) every 10."""
+@pytest.mark.parametrize("dtype,shape", [(np.float64, (400, 700, 0.02)), (np.float32, (400, 700, 0.02)),
+                                         (np.float64, (96, 2400, 0.15)), (np.float32, (1500, 200, 0.4))])
+def test_iterates_and_objective_history_match_oracle(dtype, shape):
+    """Same iteration on both sides (same steps, same order): x after 60 iterations and f(x) every 10.  The
+    wide shapes (360 and 80 nonzeros per row or column) run the passes with several warps per slice; 60
+    iterations with checks every 10 replay the captured chunk graph."""
     import torch
-    A, b, lam = _problem(3, 400, 700, 0.02, dtype)
+    m, n, density = shape
+    A, b, lam = _problem(3, m, n, density, dtype)
     d = O.default_params(A.m, A.n)
     _, _, ub, vb = O.equilibrate(A, T=30, k=1, seed=0, **d)
     op = sme.sme_op_create_csr(A.m, A.n, A.row_ptr, A.col_idx, A.vals)
