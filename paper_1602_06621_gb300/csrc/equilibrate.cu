@@ -48,6 +48,7 @@ struct StepArgs {
     uint32_t sid_out[2];    // Philox stream of the table each side writes: rows -> w, columns -> s
     int64_t blocks0;        // CTAs of the first group
     int cols_first;         // 1: the first group is the column side
+    int split[2];           // warps per slice, rows [0] / columns [1] (1, 2, 4 or 8, dividing SPC)
     int mode;               // 0: full step, 1: estimate only
     int *status;
     // Batches of matrices (block-diagonal operator): per sorted row / column the matrix id and the
@@ -166,6 +167,20 @@ struct SignAcc32 {
         }
         return ss;
     }
+    // Partial sums of one warp in shared memory, [K + 1][32] (lane-minor: no bank conflicts).
+    static constexpr int WORDS = K + 1;
+    __device__ __forceinline__ void store(float *sh, int lane) const
+    {
+#pragma unroll
+        for (int p = 0; p < K; ++p) sh[p * 32 + lane] = P[p];
+        sh[K * 32 + lane] = C;
+    }
+    __device__ __forceinline__ void add_partial(const float *sh, int lane)
+    {
+#pragma unroll
+        for (int p = 0; p < K; ++p) P[p] += sh[p * 32 + lane];
+        C += sh[K * 32 + lane];
+    }
 };
 
 // FP64: direct signed accumulation (small problems; accuracy first).
@@ -189,6 +204,17 @@ struct SignAcc64 {
         for (int p = 0; p < K; ++p) ss += acc[p] * acc[p];
         return ss;
     }
+    static constexpr int WORDS = K;
+    __device__ __forceinline__ void store(double *sh, int lane) const
+    {
+#pragma unroll
+        for (int p = 0; p < K; ++p) sh[p * 32 + lane] = acc[p];
+    }
+    __device__ __forceinline__ void add_partial(const double *sh, int lane)
+    {
+#pragma unroll
+        for (int p = 0; p < K; ++p) acc[p] += sh[p * 32 + lane];
+    }
 };
 
 template <typename real, int K>
@@ -205,7 +231,7 @@ __device__ __forceinline__ double dclip(double x, double M) { return fmin(fmax(x
 
 // ------------------------------------------------------------------ the iteration kernel
 
-template <typename real, int K, int SPC>
+template <typename real, int K, int SPC, bool SPLIT>
 __global__ void __launch_bounds__(SPC * 32) sgd_iteration(StepArgs<real> a)
 {
     constexpr int KW = (K + 31) / 32;
@@ -216,8 +242,13 @@ __global__ void __launch_bounds__(SPC * 32) sgd_iteration(StepArgs<real> a)
     const int64_t blk = first ? (int64_t)blockIdx.x : (int64_t)blockIdx.x - a.blocks0;
     const SellArgs S = cols ? a.A[1] : a.A[0];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t slice = blk * SPC + warp;
-    if (slice >= S.nslices) return;
+    // Long rows: `split` warps share a slice, each over a contiguous range of its pair steps (loads stay
+    // coalesced); their partial sums are added in warp order below.  split is the same for the whole CTA.
+    const int split = SPLIT ? (cols ? a.split[1] : a.split[0]) : 1;  // SPLIT = false: the plain kernel
+    const int part = warp % split;
+    const int64_t slice = blk * (SPC / split) + warp / split;
+    const bool valid = slice < S.nslices;
+    if (split == 1 && !valid) return;
     const int64_t r = slice * 32 + lane;
 
     SignAcc<real, K> acc;
@@ -226,8 +257,10 @@ __global__ void __launch_bounds__(SPC * 32) sgd_iteration(StepArgs<real> a)
     // Two-stage software pipeline over the row's pairs of steps: the entries of pair q+2 and the
     // table gathers of pair q+1 are in flight while pair q is accumulated.  Slice widths are
     // uniform across the warp, so every branch below is warp-uniform.
-    const int np = S.slice_w[slice] / 2;
-    const int64_t pbase = S.slice_off[slice] / 2 + lane;
+    const int np_all = valid ? S.slice_w[slice] / 2 : 0;
+    const int q_begin = np_all * part / split;
+    const int np = np_all * (part + 1) / split - q_begin;
+    const int64_t pbase = (valid ? S.slice_off[slice] / 2 : 0) + lane + (int64_t)q_begin * 32;
     const void *tab = cols ? a.tab_in[1] : a.tab_in[0];
     int c0 = 0, c1 = 0, n0 = 0, n1 = 0;
     real a0 = real(0), a1 = real(0), b0 = real(0), b1 = real(0);
@@ -267,6 +300,15 @@ __global__ void __launch_bounds__(SPC * 32) sgd_iteration(StepArgs<real> a)
     }
     (void)c0;
     (void)c1;
+    if (SPLIT && split > 1) {
+        extern __shared__ __align__(16) unsigned char sgd_partials[];
+        real *sh = reinterpret_cast<real *>(sgd_partials);
+        constexpr int WORDS = SignAcc<real, K>::WORDS;
+        acc.store(sh + (size_t)warp * WORDS * 32, lane);
+        __syncthreads();
+        if (part != 0 || !valid) return;
+        for (int q = 1; q < split; ++q) acc.add_partial(sh + (size_t)(warp + q) * WORDS * 32, lane);
+    }
     if (r >= S.rows) return;
 
     const real ss = acc.sum_sq();
@@ -398,20 +440,47 @@ static SellArgs sell_args(const Sell &S)
     return SellArgs{S.slice_off, S.slice_w, S.ent, S.val64, S.perm, S.rows, S.nslices};
 }
 
+// Shared memory for the partial sums of split slices: [SPC warps][words][32 lanes].
+template <typename real, int K>
+static size_t split_smem(int spc)
+{
+    return (size_t)spc * 32 * SignAcc<real, K>::WORDS * sizeof(real);
+}
+
+// Split slices run a separate instantiation (with the shared-memory combine), so the plain kernel keeps its
+// registers and occupancy; splitting is only used with the default slices per CTA.
 template <typename real, int K>
 static void launch_k(const StepArgs<real> &a, int spc, unsigned grid, cudaStream_t s)
 {
+    if (a.split[0] > 1 || a.split[1] > 1) {
+        sgd_iteration<real, K, DEFAULT_SPC, true><<<grid, DEFAULT_SPC * 32, split_smem<real, K>(DEFAULT_SPC), s>>>(a);
+        return;
+    }
     if (sizeof(real) == 4 && (K == 16 || K == 32)) {
         if (spc == 4) {
-            sgd_iteration<real, K, 4><<<grid, 4 * 32, 0, s>>>(a);
+            sgd_iteration<real, K, 4, false><<<grid, 4 * 32, 0, s>>>(a);
             return;
         }
         if (spc == 16) {
-            sgd_iteration<real, K, 16><<<grid, 16 * 32, 0, s>>>(a);
+            sgd_iteration<real, K, 16, false><<<grid, 16 * 32, 0, s>>>(a);
             return;
         }
     }
-    sgd_iteration<real, K, DEFAULT_SPC><<<grid, DEFAULT_SPC * 32, 0, s>>>(a);
+    sgd_iteration<real, K, DEFAULT_SPC, false><<<grid, DEFAULT_SPC * 32, 0, s>>>(a);
+}
+
+template <typename real>
+static size_t split_smem_bytes(int k, int spc)
+{
+    switch (k) {
+        case 1: return split_smem<real, 1>(spc);
+        case 2: return split_smem<real, 2>(spc);
+        case 4: return split_smem<real, 4>(spc);
+        case 8: return split_smem<real, 8>(spc);
+        case 16: return split_smem<real, 16>(spc);
+        case 32: return split_smem<real, 32>(spc);
+        default: return split_smem<real, 64>(spc);
+    }
 }
 
 template <typename real>
@@ -429,11 +498,36 @@ static void launch_iteration(const StepArgs<real> &a, int k, int spc, unsigned g
     }
 }
 
-// Launch shape chosen for probe count k: slices per CTA and which side's CTAs come first.
+// Launch shape chosen for probe count k: slices per CTA, which side's CTAs come first, and warps per slice.
 struct Shape {
     int spc = DEFAULT_SPC;
     int cols_first = 0;
+    int split[2] = {1, 1};
 };
+
+// Warps per slice: long rows are shared by several warps, so that a lane walks about 16 pair steps or fewer,
+// as far as 48 KB of shared memory for the partial sums (at the default slices per CTA) allow.  The choice
+// depends only on the operator and k; a split operator always runs the default slices per CTA, so that the
+// tuned launch shape changes scheduling only, never the order of the sums.
+static void set_split(sme_op op, int k, Shape &sh)
+{
+    const size_t bytes =
+        op->dbl ? split_smem_bytes<double>(k, DEFAULT_SPC) : split_smem_bytes<float>(k, DEFAULT_SPC);
+    for (int side = 0; side < 2; ++side) {
+        const Sell &S = side ? op->bwd : op->fwd;
+        const double steps = S.nslices > 0 ? (double)S.entries / (64.0 * (double)S.nslices) : 0.0;
+        int sp = steps >= 96 ? 8 : steps >= 48 ? 4 : steps >= 24 ? 2 : 1;
+        if (bytes > 48 * 1024) sp = 1;
+        sh.split[side] = sp;
+    }
+    if (sh.split[0] > 1 || sh.split[1] > 1) sh.spc = DEFAULT_SPC;
+}
+
+static int64_t side_blocks(const Sell &S, const Shape &sh, int side)
+{
+    const int per_cta = sh.spc / sh.split[side];
+    return (S.nslices + per_cta - 1) / per_cta;
+}
 
 static int k_slot(int k)
 {
@@ -450,12 +544,13 @@ static Shape shape_for(sme_op op, int k)
         sh.spc = op->tuned[slot].spc;
         sh.cols_first = op->tuned[slot].cols_first;
     }
+    set_split(op, k, sh);
     return sh;
 }
 
 static unsigned grid_for(sme_op op, const Shape &sh)
 {
-    return (unsigned)((op->fwd.nslices + sh.spc - 1) / sh.spc + (op->bwd.nslices + sh.spc - 1) / sh.spc);
+    return (unsigned)(side_blocks(op->fwd, sh, 0) + side_blocks(op->bwd, sh, 1));
 }
 
 template <typename real>
@@ -510,9 +605,11 @@ static StepArgs<real> base_args(sme_op op, int buf_in, const Resolved &R, uint64
     a.M = (real)R.M;
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
-    const int64_t br = (op->fwd.nslices + sh.spc - 1) / sh.spc, bc = (op->bwd.nslices + sh.spc - 1) / sh.spc;
+    const int64_t br = side_blocks(op->fwd, sh, 0), bc = side_blocks(op->bwd, sh, 1);
     a.cols_first = sh.cols_first;
     a.blocks0 = sh.cols_first ? bc : br;
+    a.split[0] = sh.split[0];
+    a.split[1] = sh.split[1];
     a.status = op->d_status;
     if (op->batch) {
         for (int side = 0; side < 2; ++side) {
@@ -678,7 +775,8 @@ static sme_status symmetric_t(sme_op op, const sme_equil_params *p, real *u, rea
     launch_load<real>(op, 0, kw, u, ub, (real *)W.u, (real *)W.ub, W.tab_u[buf], (uint32_t)tb, sid_s + 1u, p->seed, s);
     launch_load<real>(op, 1, kw, u, nullptr, (real *)W.v, nullptr, W.tab_v[buf], (uint32_t)tb, sid_s, p->seed, s);
     Shape sh;  // rows only: the default shape
-    const unsigned grid = (unsigned)((op->fwd.nslices + sh.spc - 1) / sh.spc);
+    set_split(op, k, sh);
+    const unsigned grid = (unsigned)side_blocks(op->fwd, sh, 0);
     for (int t = tb; t < tb + p->T; ++t) {
         StepArgs<real> a = base_args<real>(op, t & 1, R, p->seed, sh);
         a.eta = (real)(2.0 / (R.gamma * ((double)t + (double)p->t0 + 1.0)));
@@ -798,6 +896,7 @@ static sme_status autotune_t(sme_op op, int k, cudaStream_t s, int *spc_out, int
             Shape sh;
             sh.spc = (sizeof(real) == 4 && (k == 16 || k == 32)) ? spcs[i] : DEFAULT_SPC;
             sh.cols_first = cf;
+            set_split(op, k, sh);  // a split operator keeps the default slices per CTA
             if (sh.spc != spcs[i] && i != 1) continue;
             StepArgs<real> a = base_args<real>(op, 0, R, 0, sh);
             a.mode = 1;

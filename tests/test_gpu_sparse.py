@@ -298,3 +298,44 @@ def test_device_csr_input_and_validation():
     with pytest.raises(sme.SmeError) as ei:
         sme.sme_op_create_csr(A.m, A.n, rp, col, badv)
     assert ei.value.name == "SME_ERR_NONFINITE"
+
+
+@pytest.mark.parametrize("shape", [(64, 3000, 0.2), (3000, 64, 0.2), (4000, 2000, 0.05)])
+@pytest.mark.parametrize("k", [1, 16])
+def test_long_rows_and_columns_every_step_fp64(shape, k):
+    """Rows or columns of 100-600 nonzeros: their slices are shared by several warps (partial sums added in
+    warp order).  Every step against the oracle's step from the GPU's own state, and one estimate."""
+    m, n, density = shape
+    A = I.sparse_uniform_density(m, n, density, seed=12, mean=1.0, var=1.0)
+    op, dt = make_op(A, sme.SME_F64)
+    try:
+        worst, _ = trajectory_parity(op, dt, A, T=12, k=k, seed=3)
+        rng = np.random.default_rng(5)
+        u, v = rng.normal(0, 0.5, A.m), rng.normal(0, 0.5, A.n)
+        zu, zv = gpu_estimate(op, dt, u, v, t=4, k=k, seed=3)
+    finally:
+        sme.sme_op_destroy(op)
+    assert worst <= 1e-11, worst
+    r2, c2 = O.exact_norms_sq(A, u, v)
+    assert np.all(np.abs(zu - O.row_estimate(A, u, v, O.probe_signs(3, 4, 0, A.n, k))) <= 1e-12 * r2)
+    assert np.all(np.abs(zv - O.col_estimate(A, u, v, O.probe_signs(3, 4, 1, A.m, k))) <= 1e-12 * c2)
+
+
+@pytest.mark.parametrize("k", [1, 32])
+def test_long_rows_fp32_estimate(k):
+    """Rows of the paper's Section 4 density (1% of 1e4 columns: 100 nonzeros per row), FP32: split slices
+    against the FP64 oracle, |dz| <= 2 L eps r2 with L the longest row or column (about 130)."""
+    A = I.sparse_uniform_density(4000, 10000, 0.01, seed=13, mean=1.0, var=1.0, dtype=np.float32)
+    op, dt = make_op(A)
+    try:
+        rng = np.random.default_rng(6)
+        u, v = rng.normal(0, 0.5, A.m), rng.normal(0, 0.5, A.n)
+        zu, zv = gpu_estimate(op, dt, u.astype(np.float32), v.astype(np.float32), t=2, k=k, seed=1)
+    finally:
+        sme.sme_op_destroy(op)
+    u32, v32 = u.astype(np.float32).astype(np.float64), v.astype(np.float32).astype(np.float64)
+    r2, c2 = O.exact_norms_sq(A, u32, v32)
+    L = max(np.diff(A.row_ptr).max(), np.bincount(A.col_idx).max())
+    tol = 2 * L * 2.0 ** -24
+    assert np.all(np.abs(zu - O.row_estimate(A, u32, v32, O.probe_signs(1, 2, 0, A.n, k))) <= tol * r2)
+    assert np.all(np.abs(zv - O.col_estimate(A, u32, v32, O.probe_signs(1, 2, 1, A.m, k))) <= tol * c2)
