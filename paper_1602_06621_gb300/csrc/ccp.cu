@@ -225,60 +225,8 @@ __global__ void __launch_bounds__(LQ_THREADS) ccp_objective(Sell S, const real *
     }
 }
 
-// Launch geometry of one sliced-ELL pass with SPLIT warps per slice.
-struct Pass {
-    int split;
-    unsigned blocks;
-};
-
-static Pass pass_for(const Sell &S)
-{
-    const int sp = split_for(S);
-    const int64_t per_block = LQ_THREADS / 32 / sp;
-    return Pass{sp, (unsigned)std::max<int64_t>((S.nslices + per_block - 1) / per_block, 1)};
-}
-
-// Dispatch a kernel template over the split factor.
-#define CCP_LAUNCH(kernel, real, pass, s, ...)                                                    \
-    do {                                                                                          \
-        switch ((pass).split) {                                                                   \
-            case 8: kernel<real, 8><<<(pass).blocks, LQ_THREADS, 0, s>>>(__VA_ARGS__); break;     \
-            case 4: kernel<real, 4><<<(pass).blocks, LQ_THREADS, 0, s>>>(__VA_ARGS__); break;     \
-            case 2: kernel<real, 2><<<(pass).blocks, LQ_THREADS, 0, s>>>(__VA_ARGS__); break;     \
-            default: kernel<real, 1><<<(pass).blocks, LQ_THREADS, 0, s>>>(__VA_ARGS__); break;    \
-        }                                                                                         \
-    } while (0)
 
 static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
-
-// A CUDA graph captured once from a stream of launches (on its own stream) and destroyed with its scope;
-// exec stays null when capture is not possible, and the caller then launches directly.
-struct GraphOnce {
-    cudaGraphExec_t exec = nullptr;
-    template <typename F>
-    void capture(F &&enqueue)
-    {
-        cudaStream_t q = nullptr;
-        if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            return;
-        }
-        cudaGraph_t g = nullptr;
-        if (cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-            enqueue(q);
-            if (cudaStreamEndCapture(q, &g) == cudaSuccess && g) {
-                if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
-                cudaGraphDestroy(g);
-            }
-        }
-        cudaGetLastError();
-        cudaStreamDestroy(q);
-    }
-    ~GraphOnce()
-    {
-        if (exec) cudaGraphExecDestroy(exec);
-    }
-};
 
 static void ccp_release(CcpState *C)
 {
@@ -318,8 +266,8 @@ static sme_status power_norm_t(sme_op op, CcpState *C, int iters, double *norm, 
     const Pass pf = pass_for(F), pb = pass_for(B);
     ccp_power_init<real><<<nblk(op->n), 256, 0, s>>>(op->n, (const real *)C->e, (real *)C->xe, C->sc);
     for (int i = 0; i < iters; ++i) {
-        CCP_LAUNCH(ccp_power_rows, real, pf, s, F, (const real *)C->d, (const real *)C->xe, (real *)C->yd, C->sc);
-        CCP_LAUNCH(ccp_power_cols, real, pb, s, B, (const real *)C->e, (const real *)C->yd, (real *)C->xe,
+        SPLIT_LAUNCH(ccp_power_rows, real, pf, s, F, (const real *)C->d, (const real *)C->xe, (real *)C->yd, C->sc);
+        SPLIT_LAUNCH(ccp_power_cols, real, pb, s, B, (const real *)C->e, (const real *)C->yd, (real *)C->xe,
                    C->partials, C->counter, C->sc);
     }
     *launches += 1 + 2 * (int64_t)iters;
@@ -389,12 +337,12 @@ static sme_status ccp_t(sme_op op, const real *ubar, const real *vbar, const rea
     // A chunk of `every` iterations and its objective check, all on fixed buffers.
     auto enqueue_chunk = [&](int64_t chunk, cudaStream_t q) {
         for (int64_t j = 0; j < chunk; ++j) {
-            CCP_LAUNCH(ccp_rows, real, pf, q, F, d, bs, xe, y, yd, C->sc);
-            CCP_LAUNCH(ccp_cols, real, pb, q, B, e, yd, xs, xe, C->counter, C->sc);
+            SPLIT_LAUNCH(ccp_rows, real, pf, q, F, d, bs, xe, y, yd, C->sc);
+            SPLIT_LAUNCH(ccp_cols, real, pb, q, B, e, yd, xs, xe, C->counter, C->sc);
         }
         ccp_current_x<real><<<nblk(n), 256, 0, q>>>(n, e, xs, xt, nullptr, nullptr, C->partials, C->counter, C->sc,
                                                    0);
-        CCP_LAUNCH(ccp_objective, real, pf, q, F, xt, bs, C->partials, C->counter, C->sc, 0);
+        SPLIT_LAUNCH(ccp_objective, real, pf, q, F, xt, bs, C->partials, C->counter, C->sc, 0);
     };
     // Full chunks are captured once as a CUDA graph and replayed (on a private stream: the caller's may be
     // the legacy default stream, which cannot be captured); without a graph they are launched directly.
@@ -429,7 +377,7 @@ static sme_status ccp_t(sme_op op, const real *ubar, const real *vbar, const rea
         stop = C->host->done != 0;
     }
     ccp_current_x<real><<<nblk(n), 256, 0, s>>>(n, e, xs, xt, B.perm, x_out, C->partials, C->counter, C->sc, 1);
-    CCP_LAUNCH(ccp_objective, real, pf, s, F, xt, bs, C->partials, C->counter, C->sc, 1);
+    SPLIT_LAUNCH(ccp_objective, real, pf, s, F, xt, bs, C->partials, C->counter, C->sc, 1);
     launches += 2;
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(C->host, C->sc, sizeof(CcpScalars), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -372,21 +372,20 @@ __global__ void lsqr_init_rows(int64_t m, const int32_t *perm, const real *b, co
 }
 
 // Products with A (rows): uhat = K v_i - alpha_i u_i; beta_{i+1} = ||uhat||.
-template <typename real>
+template <typename real, int SPLIT>
 __global__ void __launch_bounds__(LQ_THREADS) lsqr_rows(Sell S, const real *d, const real *ve, real *ud,
                                                          double *partials, unsigned *counter, LsqrScalars *sc)
 {
-    if (((volatile LsqrScalars *)sc)->done) return;
+    if (((volatile LsqrScalars *)sc)->done) return;  // the same for every thread of the block
     const double alpha = sc->alpha, beta = sc->beta;
     const real inv_alpha = (real)(alpha > 0.0 ? 1.0 / alpha : 0.0);
     const real alpha_r = (real)alpha;
     const real inv_beta = (real)(beta > 0.0 ? 1.0 / beta : 0.0);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
+    const SplitSlice<SPLIT> sw;
+    const real acc = sell_row_dot_split<real, real, real, SPLIT>(S, sw, ve);
     double part = 0.0;
-    if (slice < S.nslices) {
-        const real acc = sell_row_dot<real, real, real>(S, slice, lane, ve);
-        const int64_t r = slice * 32 + lane;
+    if (sw.lead() && sw.slice < S.nslices) {
+        const int64_t r = sw.slice * 32 + sw.lane;
         if (r < S.rows) {
             const real dr = d[r];
             const real uhat = dr * acc * inv_alpha - alpha_r * (ud[r] / dr) * inv_beta;
@@ -402,12 +401,12 @@ __global__ void __launch_bounds__(LQ_THREADS) lsqr_rows(Sell S, const real *d, c
 // Products with A^T (columns): the lagged x/w update of the previous iteration, then
 // vhat = K^T u_{i+1} - beta_{i+1} v_i, alpha_{i+1} = ||vhat||, and the scalar recurrence of iteration i.
 // init = 1 computes vhat = K^T u_1 only (alpha_1, rhobar_1).
-template <typename real>
+template <typename real, int SPLIT>
 __global__ void __launch_bounds__(LQ_THREADS) lsqr_cols(Sell S, const real *e, const real *ud, real *ve, real *w,
                                                          real *x, double *partials, unsigned *counter,
                                                          LsqrScalars *sc, int init)
 {
-    if (((volatile LsqrScalars *)sc)->done) return;
+    if (((volatile LsqrScalars *)sc)->done) return;  // the same for every thread of the block
     const double alpha = sc->alpha, beta = sc->beta;
     const int first = sc->first;
     const real inv_alpha = (real)(alpha > 0.0 ? 1.0 / alpha : 0.0);
@@ -415,12 +414,11 @@ __global__ void __launch_bounds__(LQ_THREADS) lsqr_cols(Sell S, const real *e, c
     const real beta_r = (real)beta;
     const real x_step = (real)(sc->phi / sc->rho);
     const real w_step = (real)(sc->theta / sc->rho);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
+    const SplitSlice<SPLIT> sw;
+    const real acc = sell_row_dot_split<real, real, real, SPLIT>(S, sw, ud);
     double part = 0.0;
-    if (slice < S.nslices) {
-        const real acc = sell_row_dot<real, real, real>(S, slice, lane, ud);
-        const int64_t c = slice * 32 + lane;
+    if (sw.lead() && sw.slice < S.nslices) {
+        const int64_t c = sw.slice * 32 + sw.lane;
         if (c < S.rows) {
             const real ec = e[c];
             real vhat;
@@ -483,18 +481,17 @@ __global__ void lsqr_current_x(int64_t n, const real *e, const real *x, const re
 }
 
 // r = A xt - b in FP64 (rows); ||r|| / ||b|| against tol (stop_rule 0).
-template <typename real>
+template <typename real, int SPLIT>
 __global__ void __launch_bounds__(LQ_THREADS) lsqr_residual(Sell S, const real *xt, const real *bs, double *r,
                                                              double *partials, unsigned *counter, LsqrScalars *sc,
                                                              int final_check)
 {
-    if (!final_check && ((volatile LsqrScalars *)sc)->done == 1) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
+    if (!final_check && ((volatile LsqrScalars *)sc)->done == 1) return;  // uniform over the block
+    const SplitSlice<SPLIT> sw;
+    const double acc = sell_row_dot_split<real, double, real, SPLIT>(S, sw, xt);
     double part = 0.0;
-    if (slice < S.nslices) {
-        const double acc = sell_row_dot<real, double, real>(S, slice, lane, xt);
-        const int64_t i = slice * 32 + lane;
+    if (sw.lead() && sw.slice < S.nslices) {
+        const int64_t i = sw.slice * 32 + sw.lane;
         if (i < S.rows) {
             const double ri = acc - (double)bs[i];
             r[i] = ri;
@@ -510,18 +507,15 @@ __global__ void __launch_bounds__(LQ_THREADS) lsqr_residual(Sell S, const real *
 }
 
 // ||A^T r|| / (||A||_F ||r||) (columns), FP64.
-template <typename real>
+template <typename real, int SPLIT>
 __global__ void __launch_bounds__(LQ_THREADS) lsqr_normal(Sell S, const double *r, double *partials,
                                                            unsigned *counter, LsqrScalars *sc, int final_check)
 {
-    if (!final_check && ((volatile LsqrScalars *)sc)->done == 1) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
+    if (!final_check && ((volatile LsqrScalars *)sc)->done == 1) return;  // uniform over the block
+    const SplitSlice<SPLIT> sw;
+    const double acc = sell_row_dot_split<real, double, double, SPLIT>(S, sw, r);
     double part = 0.0;
-    if (slice < S.nslices) {
-        const double acc = sell_row_dot<real, double, double>(S, slice, lane, r);
-        if (slice * 32 + lane < S.rows) part = acc * acc;
-    }
+    if (sw.lead() && sw.slice < S.nslices && sw.slice * 32 + sw.lane < S.rows) part = acc * acc;
     if (!arrive_last(part, partials, counter)) return;
     const double tot = sum_partials(partials, counter);
     if (threadIdx.x != 0) return;
@@ -582,7 +576,8 @@ static sme_status ensure_lsqr(sme_op op, cudaStream_t s)
     const int64_t m = op->m, n = op->n;
     L->fwd_blocks = (op->fwd.nslices + 7) / 8;
     L->bwd_blocks = (op->bwd.nslices + 7) / 8;
-    const int64_t maxb = std::max<int64_t>(std::max(L->fwd_blocks, L->bwd_blocks), (std::max(m, n) + 255) / 256);
+    // One partial per block of any pass: at most one block per slice (8 warps on one slice).
+    const int64_t maxb = std::max<int64_t>(std::max(op->fwd.nslices, op->bwd.nslices), (std::max(m, n) + 255) / 256);
     SME_TRY(dev_alloc(op, &L->ud, m * sz));
     SME_TRY(dev_alloc(op, &L->bs, m * sz));
     SME_TRY(dev_alloc(op, &L->d, m * sz));
@@ -611,7 +606,8 @@ static sme_status lsqr_t(sme_op op, const real *ubar, const real *vbar, const re
     const Sell &F = op->fwd, &B = op->bwd;
     real *ud = (real *)L->ud, *ve = (real *)L->ve, *w = (real *)L->w, *x = (real *)L->x;
     real *d = (real *)L->d, *e = (real *)L->e, *bs = (real *)L->bs, *xt = (real *)L->xt;
-    const unsigned fb = (unsigned)std::max<int64_t>(L->fwd_blocks, 1), bb = (unsigned)std::max<int64_t>(L->bwd_blocks, 1);
+    const unsigned fb = (unsigned)std::max<int64_t>(L->fwd_blocks, 1);
+    const Pass pf = pass_for(F), pb = pass_for(B);
     int64_t launches = 0;
     LsqrScalars init{};
     init.tol = p->tol;
@@ -634,25 +630,32 @@ static sme_status lsqr_t(sme_op op, const real *ubar, const real *vbar, const re
     scales_sorted<real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, B.perm, vbar, e);
     lsqr_init_rows<real><<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, F.perm, b, d, bs, ud, L->partials,
                                                                        L->counter, L->sc);
-    lsqr_cols<real><<<bb, LQ_THREADS, 0, s>>>(B, e, ud, ve, w, x, L->partials, L->counter, L->sc, 1);
+    SPLIT_LAUNCH(lsqr_cols, real, pb, s, B, e, ud, ve, w, x, L->partials, L->counter, L->sc, 1);
     launches += 4;
     SME_CUDA(cudaGetLastError());
     const int every = std::max(1, p->check_every);
+    // A chunk of `every` iterations and its residual check, on fixed buffers: captured once as a CUDA graph
+    // (on a private stream) and replayed; partial chunks and graph-less runs launch directly.
+    auto enqueue_chunk = [&](int64_t chunk, cudaStream_t q) {
+        for (int64_t j = 0; j < chunk; ++j) {
+            SPLIT_LAUNCH(lsqr_rows, real, pf, q, F, d, ve, ud, L->partials, L->counter, L->sc);
+            SPLIT_LAUNCH(lsqr_cols, real, pb, q, B, e, ud, ve, w, x, L->partials, L->counter, L->sc, 0);
+        }
+        lsqr_current_x<real><<<(unsigned)((n + 255) / 256), 256, 0, q>>>(n, e, x, w, L->sc, xt, nullptr, nullptr);
+        SPLIT_LAUNCH(lsqr_residual, real, pf, q, F, xt, bs, L->r, L->partials, L->counter, L->sc, 0);
+        if (p->stop_rule == 1) SPLIT_LAUNCH(lsqr_normal, real, pb, q, B, L->r, L->partials, L->counter, L->sc, 0);
+    };
+    GraphOnce chunk_graph;
+    if (p->max_iters >= 2 * (int64_t)every) chunk_graph.capture([&](cudaStream_t q) { enqueue_chunk(every, q); });
     int64_t it = 0;
     while (it < p->max_iters) {
         const int64_t chunk = std::min<int64_t>(every, p->max_iters - it);
-        for (int64_t j = 0; j < chunk; ++j) {
-            lsqr_rows<real><<<fb, LQ_THREADS, 0, s>>>(F, d, ve, ud, L->partials, L->counter, L->sc);
-            lsqr_cols<real><<<bb, LQ_THREADS, 0, s>>>(B, e, ud, ve, w, x, L->partials, L->counter, L->sc, 0);
-        }
+        if (chunk == every && chunk_graph.exec)
+            SME_CUDA(cudaGraphLaunch(chunk_graph.exec, s));
+        else
+            enqueue_chunk(chunk, s);
         it += chunk;
-        lsqr_current_x<real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, e, x, w, L->sc, xt, nullptr, nullptr);
-        lsqr_residual<real><<<fb, LQ_THREADS, 0, s>>>(F, xt, bs, L->r, L->partials, L->counter, L->sc, 0);
-        launches += 2 * chunk + 2;
-        if (p->stop_rule == 1) {
-            lsqr_normal<real><<<bb, LQ_THREADS, 0, s>>>(B, L->r, L->partials, L->counter, L->sc, 0);
-            ++launches;
-        }
+        launches += 2 * chunk + 2 + (p->stop_rule == 1 ? 1 : 0);
         SME_CUDA(cudaGetLastError());
         SME_CUDA(cudaMemcpyAsync(L->host, L->sc, sizeof(LsqrScalars), cudaMemcpyDeviceToHost, s));
         SME_CUDA(cudaStreamSynchronize(s));
@@ -660,8 +663,8 @@ static sme_status lsqr_t(sme_op op, const real *ubar, const real *vbar, const re
     }
     // Final x in original order, and both residuals of exactly that x.
     lsqr_current_x<real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, e, x, w, L->sc, xt, B.perm, x_out);
-    lsqr_residual<real><<<fb, LQ_THREADS, 0, s>>>(F, xt, bs, L->r, L->partials, L->counter, L->sc, 1);
-    lsqr_normal<real><<<bb, LQ_THREADS, 0, s>>>(B, L->r, L->partials, L->counter, L->sc, 1);
+    SPLIT_LAUNCH(lsqr_residual, real, pf, s, F, xt, bs, L->r, L->partials, L->counter, L->sc, 1);
+    SPLIT_LAUNCH(lsqr_normal, real, pb, s, B, L->r, L->partials, L->counter, L->sc, 1);
     launches += 3;
     SME_CUDA(cudaGetLastError());
     SME_CUDA(cudaMemcpyAsync(L->host, L->sc, sizeof(LsqrScalars), cudaMemcpyDeviceToHost, s));

@@ -3,6 +3,8 @@
 // dot product of one sliced-ELL row with a gathered vector.
 #pragma once
 
+#include <algorithm>
+
 #include "sme_internal.cuh"
 
 namespace sme {
@@ -171,5 +173,58 @@ inline int split_for(const Sell &S)
     const double steps = S.nslices > 0 ? (double)S.entries / (64.0 * (double)S.nslices) : 0.0;
     return steps >= 96 ? 8 : steps >= 48 ? 4 : steps >= 24 ? 2 : 1;
 }
+
+// Launch geometry of one sliced-ELL pass with SPLIT warps per slice.
+struct Pass {
+    int split;
+    unsigned blocks;
+};
+
+inline Pass pass_for(const Sell &S)
+{
+    const int sp = split_for(S);
+    const int64_t per_block = LQ_THREADS / 32 / sp;
+    return Pass{sp, (unsigned)std::max<int64_t>((S.nslices + per_block - 1) / per_block, 1)};
+}
+
+// Dispatch a kernel template over the split factor.
+#define SPLIT_LAUNCH(kernel, real, pass, s, ...)                                                    \
+    do {                                                                                          \
+        switch ((pass).split) {                                                                   \
+            case 8: kernel<real, 8><<<(pass).blocks, LQ_THREADS, 0, s>>>(__VA_ARGS__); break;     \
+            case 4: kernel<real, 4><<<(pass).blocks, LQ_THREADS, 0, s>>>(__VA_ARGS__); break;     \
+            case 2: kernel<real, 2><<<(pass).blocks, LQ_THREADS, 0, s>>>(__VA_ARGS__); break;     \
+            default: kernel<real, 1><<<(pass).blocks, LQ_THREADS, 0, s>>>(__VA_ARGS__); break;    \
+        }                                                                                         \
+    } while (0)
+
+// A CUDA graph captured once from a stream of launches (on its own stream) and destroyed with its scope;
+// exec stays null when capture is not possible, and the caller then launches directly.
+struct GraphOnce {
+    cudaGraphExec_t exec = nullptr;
+    template <typename F>
+    void capture(F &&enqueue)
+    {
+        cudaStream_t q = nullptr;
+        if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            enqueue(q);
+            if (cudaStreamEndCapture(q, &g) == cudaSuccess && g) {
+                if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
+                cudaGraphDestroy(g);
+            }
+        }
+        cudaGetLastError();
+        cudaStreamDestroy(q);
+    }
+    ~GraphOnce()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+    }
+};
 
 }  // namespace sme
