@@ -116,6 +116,50 @@ def recorded_traffic():
         return None
 
 
+class Ranks:
+    """The job's ranks: one process per GPU, each equilibrating its own matrix (weak scaling, no data-path
+    collective).  The only collectives are the timing barrier and the max over ranks of elapsed times."""
+
+    def __init__(self, rank, world, local, backend="nccl"):
+        self.rank, self.world, self.local, self.backend = rank, world, local, backend
+        self.dist = None
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            kw = {"device_id": torch.device("cuda", local)} if backend == "nccl" else {}
+            dist.init_process_group(backend, rank=rank, world_size=world, **kw)
+            self.dist = dist
+
+    def _device(self):
+        return f"cuda:{self.local}" if self.backend == "nccl" else "cpu"
+
+    def barrier(self):
+        import torch
+        if self.dist is not None:
+            self.dist.barrier()
+        if self.backend == "nccl":
+            torch.cuda.synchronize()
+
+    def max(self, x: float) -> float:
+        """The largest value over ranks (every rank gets it)."""
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([x], device=self._device(), dtype=torch.float64)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def rank_matrix_seed(rank: int) -> int:
+    """Seed of the large workload's matrix on this rank: every rank equilibrates a different matrix."""
+    return 2 + rank
+
+
 class ClockSampler:
     """nvidia-smi clock and throttle-reason samples during the timed region."""
 
@@ -789,18 +833,11 @@ def main():
     from paper_1602_06621_gb300 import sme
 
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
+    ranks = Ranks(rank, world, local)
+    barrier = ranks.barrier
 
     k, T = args.k, args.T
-    A = I.workload_large(args.scale, seed=2 + rank)
+    A = I.workload_large(args.scale, seed=rank_matrix_seed(rank))
     m, n, nnz = A.m, A.n, A.nnz
     op = sme.sme_op_create_csr(m, n, A.row_ptr, A.col_idx, A.vals)
     f32 = dict(dtype=torch.float32, device="cuda")
@@ -853,11 +890,7 @@ def main():
         ev1.record(stream)
         barrier()
     sme.sme_op_check(op)
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    if dist is not None:
-        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = ranks.max(ev0.elapsed_time(ev1) / 1e3)
     clocks = clk.summary()
 
     units_per_step = k * T
@@ -910,11 +943,7 @@ def main():
             torch.cuda.synchronize()
             sme.sme_op_destroy(op2)
         barrier()
-        e2e_el = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([e2e_el], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_el = float(t.item())
+        e2e_el = ranks.max(time.perf_counter() - t0)
         h2d = 4 * (m + 1) + 8 * nnz + 4 * m  # CSR arrays + b
         e2e = {"value": world * units_per_step * e2e_steps / e2e_el, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 4 * (m + 2 * n), "steps": e2e_steps, "ms_per_step": 1e3 * e2e_el / e2e_steps}
@@ -962,8 +991,7 @@ def main():
                             "plain": plain}
         print(json.dumps(line), flush=True)
     sme.sme_op_destroy(op)
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
     return 0
 
 
