@@ -45,7 +45,7 @@ typedef enum {
     SME_ERR_NONFINITE = -5,     /* a NaN or Inf in the input values or in an iterate */
     SME_ERR_TIMEOUT = -6,       /* a bounded device-side wait gave up */
     SME_ERR_NOT_CONVERGED = -7, /* LSQR stopped at max_iters above its tolerance (results still written) */
-    SME_ERR_UNSUPPORTED = -8    /* a valid request this build does not implement (e.g. an unsupported k) */
+    SME_ERR_UNSUPPORTED = -8    /* a valid request the library does not implement (e.g. an unsupported k) */
 } sme_status;
 
 typedef enum {
