@@ -97,22 +97,23 @@ extern "C" sme_status sme_batch_create(sme_batch *out, int32_t count, const int6
         }
     }
     rp[M] = (int32_t)NNZ;
-    // Matrices are grouped in order so that each group's gather tables (8 bytes per row and per column) stay
-    // within L2_GROUP_BYTES; rows and columns are then laid out group-major, so the CTAs running at any
-    // moment gather from one group's tables and those stay L2-resident (one group per matrix when a single
-    // matrix is larger).
-    // SME_BATCH_GROUP_BYTES overrides the budget (tests use a small one to exercise grouping).
-    int64_t L2_GROUP_BYTES = 32ll << 20;
+    // Rows and columns are laid out group-major (then by length), so the CTAs running at any moment gather
+    // from one group's tables and those stay cached.  By default every matrix is its own group: its slices
+    // then form one contiguous range (at most one partially filled slice per matrix), which also lets
+    // per-matrix work such as LSQR skip finished matrices' slices altogether.  SME_BATCH_GROUP_BYTES > 0
+    // packs consecutive matrices into groups whose gather tables (8 bytes per row and per column) fit that
+    // many bytes instead.
+    int64_t group_bytes = 0;
     if (const char *env = std::getenv("SME_BATCH_GROUP_BYTES")) {
         const long long v = std::atoll(env);
-        if (v > 0) L2_GROUP_BYTES = v;
+        if (v > 0) group_bytes = v;
     }
     std::vector<uint32_t> gr(M), gc(N);
     uint32_t g = 0;
     int64_t acc = 0;
     for (int32_t b = 0; b < count; ++b) {
         const int64_t bytes = 8 * (m[b] + n[b]);
-        if (acc > 0 && acc + bytes > L2_GROUP_BYTES) {
+        if (b > 0 && (group_bytes == 0 || acc + bytes > group_bytes)) {
             ++g;
             acc = 0;
         }
@@ -131,6 +132,7 @@ extern "C" sme_status sme_batch_create(sme_batch *out, int32_t count, const int6
     BatchInfo *B = new BatchInfo();
     op->batch = B;
     B->count = count;
+    B->matrix_major = group_bytes == 0 && count > 1 && op->fwd.grouped && op->bwd.grouped;
     B->row_off = new int64_t[count + 1];
     B->col_off = new int64_t[count + 1];
     std::memcpy(B->row_off, roff.data(), (count + 1) * sizeof(int64_t));

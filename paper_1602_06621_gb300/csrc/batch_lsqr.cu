@@ -32,9 +32,17 @@ struct BLsqr {
     double *sq_r = nullptr, *sq_c = nullptr, *sq_r2 = nullptr, *r = nullptr;
     int64_t *roff = nullptr, *coff = nullptr;  // device copies of the batch offsets
     BScal *sc = nullptr, *host = nullptr;
+    int32_t *list_r = nullptr, *list_c = nullptr;  // slices of unfinished matrices (matrix-major layout)
 };
 
 // ------------------------------------------------------------------ kernels
+
+// The slice a warp takes: its own index, or an entry of a list of the slices still at work (slices of
+// matrices that have not converged); past the end of the list, no slice.
+__device__ __forceinline__ int64_t listed_slice(const int32_t *list, int64_t nlist, int64_t idx)
+{
+    return list ? (idx < nlist ? (int64_t)list[idx] : INT64_MAX) : idx;
+}
 
 template <typename real>
 __global__ void bl_init_rows(int64_t M, const int32_t *perm, const real *bvec, const real *d, real *bs, real *ud,
@@ -52,10 +60,11 @@ __global__ void bl_init_rows(int64_t M, const int32_t *perm, const real *bvec, c
 
 template <typename real>
 __global__ void __launch_bounds__(LQ_THREADS) bl_rows(Sell S, const int32_t *mid, const real *d, const real *ve,
-                                                       real *ud, double *sq, const BScal *sc)
+                                                       real *ud, double *sq, const BScal *sc, const int32_t *list,
+                                                       int64_t nlist)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
+    const int64_t slice = listed_slice(list, nlist, (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp);
     if (slice >= S.nslices) return;
     const int64_t r = slice * 32 + lane;
     // Rows of finished matrices (and padding rows) do no work.
@@ -74,10 +83,10 @@ __global__ void __launch_bounds__(LQ_THREADS) bl_rows(Sell S, const int32_t *mid
 template <typename real>
 __global__ void __launch_bounds__(LQ_THREADS) bl_cols(Sell S, const int32_t *mid, const real *e, const real *ud,
                                                        real *ve, real *w, real *x, double *sq, const BScal *sc,
-                                                       int init)
+                                                       int init, const int32_t *list, int64_t nlist)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
+    const int64_t slice = listed_slice(list, nlist, (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp);
     if (slice >= S.nslices) return;
     const int64_t c = slice * 32 + lane;
     const bool live = c < S.rows && !sc[mid[c]].done;
@@ -198,10 +207,11 @@ __global__ void bl_current_x(int64_t N, const int32_t *mid, const int32_t *perm,
 // skipped: their partial sums are not read again before the final pass, which computes every row.
 template <typename real>
 __global__ void __launch_bounds__(LQ_THREADS) bl_residual(Sell S, const int32_t *mid, const BScal *sc, int skip_done,
-                                                           const real *xt, const real *bs, double *r, double *sq)
+                                                           const real *xt, const real *bs, double *r, double *sq,
+                                                           const int32_t *list, int64_t nlist)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t slice = (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp;
+    const int64_t slice = listed_slice(list, nlist, (int64_t)blockIdx.x * (LQ_THREADS / 32) + warp);
     if (slice >= S.nslices) return;
     const int64_t i = slice * 32 + lane;
     const bool live = i < S.rows && !(skip_done && sc[mid[i]].done == 1);
@@ -256,7 +266,8 @@ static void bl_release(BLsqr *L)
 {
     if (!L) return;
     for (void *p : {L->ud, L->ve, L->w, L->x, L->d, L->e, L->bs, L->xt, (void *)L->sq_r, (void *)L->sq_c,
-                    (void *)L->sq_r2, (void *)L->r, (void *)L->roff, (void *)L->coff, (void *)L->sc})
+                    (void *)L->sq_r2, (void *)L->r, (void *)L->roff, (void *)L->coff, (void *)L->sc,
+                    (void *)L->list_r, (void *)L->list_c})
         if (p) cudaFree(p);
     if (L->host) cudaFreeHost(L->host);
     delete L;
@@ -305,24 +316,49 @@ static sme_status batch_lsqr_t(sme_op op, const real *ubar, const real *vbar, co
     bl_scales<real><<<nblk(N), 256, 0, s>>>(N, Bk.perm, vbar, e);
     bl_init_rows<real><<<nblk(M), 256, 0, s>>>(M, F.perm, bvec, d, bs, ud, L->sq_r, L->sq_r2);
     bl_reduce<<<count, LQ_THREADS, 0, s>>>(L->sq_r, L->sq_r2, L->roff, L->sc, RED_INIT_BETA, p->tol, p->stop_rule, 0);
-    bl_cols<real><<<bb, LQ_THREADS, 0, s>>>(Bk, mid_c, e, ud, ve, w, x, L->sq_c, L->sc, 1);
+    bl_cols<real><<<bb, LQ_THREADS, 0, s>>>(Bk, mid_c, e, ud, ve, w, x, L->sq_c, L->sc, 1, nullptr, 0);
     bl_reduce<<<count, LQ_THREADS, 0, s>>>(L->sq_c, nullptr, L->coff, L->sc, RED_INIT_ALPHA, p->tol, p->stop_rule, 0);
     launches += 8;
     SME_CUDA(cudaGetLastError());
     const int every = std::max(1, p->check_every);
+    // With one group per matrix, matrix b's rows are sorted positions row_off[b] .. row_off[b+1]-1 (columns
+    // likewise), so once some matrices have converged the products run over the slices of the others only.
+    const bool compact = B->matrix_major;
+    std::vector<int32_t> lr, lc;
+    std::vector<char> active_prev(count, 1);
+    int64_t nlr = 0, nlc = 0;
+    unsigned gr = fb, gc = bb;
+    if (compact) {
+        if (cudaMalloc(&L->list_r, F.nslices * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&L->list_c, Bk.nslices * sizeof(int32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SME_ERR_OOM);
+        }
+    }
+    auto slices_of_active = [&](const int64_t *off, std::vector<int32_t> &out) {
+        out.clear();
+        int64_t last = -1;
+        for (int b = 0; b < count; ++b) {
+            if (L->host[b].done) continue;
+            const int64_t s0 = std::max<int64_t>(off[b] / 32, last + 1), s1 = (off[b + 1] + 31) / 32;
+            for (int64_t q = s0; q < s1; ++q) out.push_back((int32_t)q);
+            last = std::max<int64_t>(last, s1 - 1);
+        }
+    };
+    const int32_t *use_lr = nullptr, *use_lc = nullptr;
     int64_t it = 0;
     bool all_done = false;
     while (it < p->max_iters && !all_done) {
         const int64_t chunk = std::min<int64_t>(every, p->max_iters - it);
         for (int64_t j = 0; j < chunk; ++j) {
-            bl_rows<real><<<fb, LQ_THREADS, 0, s>>>(F, mid_r, d, ve, ud, L->sq_r, L->sc);
+            bl_rows<real><<<gr, LQ_THREADS, 0, s>>>(F, mid_r, d, ve, ud, L->sq_r, L->sc, use_lr, nlr);
             bl_reduce<<<count, LQ_THREADS, 0, s>>>(L->sq_r, nullptr, L->roff, L->sc, RED_BETA, p->tol, p->stop_rule, 0);
-            bl_cols<real><<<bb, LQ_THREADS, 0, s>>>(Bk, mid_c, e, ud, ve, w, x, L->sq_c, L->sc, 0);
+            bl_cols<real><<<gc, LQ_THREADS, 0, s>>>(Bk, mid_c, e, ud, ve, w, x, L->sq_c, L->sc, 0, use_lc, nlc);
             bl_reduce<<<count, LQ_THREADS, 0, s>>>(L->sq_c, nullptr, L->coff, L->sc, RED_ALPHA, p->tol, p->stop_rule, 0);
         }
         it += chunk;
         bl_current_x<real><<<nblk(N), 256, 0, s>>>(N, mid_c, Bk.perm, e, x, w, L->sc, xt, nullptr, 1);
-        bl_residual<real><<<fb, LQ_THREADS, 0, s>>>(F, mid_r, L->sc, 1, xt, bs, L->r, L->sq_r);
+        bl_residual<real><<<gr, LQ_THREADS, 0, s>>>(F, mid_r, L->sc, 1, xt, bs, L->r, L->sq_r, use_lr, nlr);
         bl_reduce<<<count, LQ_THREADS, 0, s>>>(L->sq_r, nullptr, L->roff, L->sc, RED_RESID, p->tol, p->stop_rule, 0);
         launches += 4 * chunk + 3;
         if (p->stop_rule == 1) {
@@ -334,10 +370,29 @@ static sme_status batch_lsqr_t(sme_op op, const real *ubar, const real *vbar, co
         SME_CUDA(cudaMemcpyAsync(L->host, L->sc, count * sizeof(BScal), cudaMemcpyDeviceToHost, s));
         SME_CUDA(cudaStreamSynchronize(s));
         all_done = true;
-        for (int b = 0; b < count; ++b) all_done = all_done && L->host[b].done != 0;
+        bool changed = false;
+        for (int b = 0; b < count; ++b) {
+            const char act = L->host[b].done == 0;
+            all_done = all_done && !act;
+            changed = changed || act != active_prev[b];
+            active_prev[b] = act;
+        }
+        if (compact && changed && !all_done) {
+            slices_of_active(B->row_off, lr);
+            slices_of_active(B->col_off, lc);
+            nlr = (int64_t)lr.size();
+            nlc = (int64_t)lc.size();
+            SME_CUDA(cudaMemcpyAsync(L->list_r, lr.data(), nlr * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            SME_CUDA(cudaMemcpyAsync(L->list_c, lc.data(), nlc * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            SME_CUDA(cudaStreamSynchronize(s));  // the host vectors may change before the copies complete
+            use_lr = L->list_r;
+            use_lc = L->list_c;
+            gr = (unsigned)std::max<int64_t>((nlr + 7) / 8, 1);
+            gc = (unsigned)std::max<int64_t>((nlc + 7) / 8, 1);
+        }
     }
     bl_current_x<real><<<nblk(N), 256, 0, s>>>(N, mid_c, Bk.perm, e, x, w, L->sc, xt, x_out, 0);
-    bl_residual<real><<<fb, LQ_THREADS, 0, s>>>(F, mid_r, L->sc, 0, xt, bs, L->r, L->sq_r);
+    bl_residual<real><<<fb, LQ_THREADS, 0, s>>>(F, mid_r, L->sc, 0, xt, bs, L->r, L->sq_r, nullptr, 0);
     bl_reduce<<<count, LQ_THREADS, 0, s>>>(L->sq_r, nullptr, L->roff, L->sc, RED_RESID, p->tol, p->stop_rule, 1);
     bl_normal<real><<<bb, LQ_THREADS, 0, s>>>(Bk, L->r, L->sq_c);
     bl_reduce<<<count, LQ_THREADS, 0, s>>>(L->sq_c, nullptr, L->coff, L->sc, RED_NORMAL, p->tol, p->stop_rule, 1);

@@ -421,6 +421,7 @@ static sme_status make_sell(sme_op op, Sell &S, int64_t rows, const int32_t *ptr
     // Rows in descending length (stable), group-major when groups are given and the key fits 32 bits.
     const int len_bits = std::max(1, bit_length((uint64_t)maxlen));
     if (group && len_bits + group_bits > 32) group = nullptr;
+    S.grouped = group != nullptr;
     length_keys<<<nblk(rows), 256, 0, s>>>(len_orig, rows, maxlen, group, len_bits, k0, S.perm);
     bool alt = false;
     SME_TRY(radix_sort_pairs(k0, S.perm, k1, v1, rows, group ? len_bits + group_bits : bit_length((uint64_t)maxlen),

@@ -130,6 +130,7 @@ struct Sell {
     int32_t *len = nullptr;        // [rows] length at each sorted position
     void *ent = nullptr;           // see above
     double *val64 = nullptr;       // FP64 values (double2 pairs), FP64 ops only
+    bool grouped = false;          // rows ordered group-major (see build_sparse)
 };
 
 struct Workspace {
@@ -165,6 +166,9 @@ struct BatchInfo {
     void *tgt2[2] = {nullptr, nullptr};    // per matrix alpha^2 [0], beta^2 [1] (state type)
     uint32_t sid_base = 0;                 // Philox stream of matrix b: sid_base + 2b (s), + 2b + 1 (w)
     int64_t *row_off = nullptr, *col_off = nullptr;  // host, count + 1
+    // One group per matrix on both sides: matrix b's rows then occupy sorted positions row_off[b] ..
+    // row_off[b+1]-1 (columns likewise), so its slices form one contiguous range.
+    bool matrix_major = false;
 };
 
 }  // namespace sme
