@@ -32,8 +32,20 @@ if ROOT not in sys.path:
 METRIC = "equilibration probe-pairs/s + HBM GB/s; time to LSQR 1e-6 vs plain, 1×GB300"
 UNIT = "probe-pairs/s"
 FALLBACK_HBM_GBS = 6800.0
-# The iteration kernel's sources: recorded ncu traffic is used only while these are unchanged.
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_1602_06621_gb300", "csrc", f) for f in ("equilibrate.cu", "sme_internal.cuh")]
+# The iteration kernel's code: its source file and the device code it uses from the internal header (the
+# Philox section).  Recorded ncu traffic is used only while these are unchanged.
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1602_06621_gb300", "csrc", "equilibrate.cu")
+KERNEL_HEADER = os.path.join(ROOT, "paper_1602_06621_gb300", "csrc", "sme_internal.cuh")
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    h.update(open(KERNEL_SOURCE, "rb").read())
+    header = open(KERNEL_HEADER, "rb").read()
+    start = header.find(b"Philox4x32-10")
+    end = header.find(b"------ operator", start)
+    h.update(header[start:end] if start >= 0 and end > start else header)
+    return h.hexdigest()
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sgd_iteration_f32_k32_large.txt")
 # Random 8-byte gathers per second from L2-resident tables, measured on GB300 by
 # paper_1602_06621_gb300/microbench/gather_ceiling.cu (profiles/sgd_iteration_f32_k32_large.txt): the second
@@ -100,10 +112,7 @@ def measured_hbm_peak():
 def recorded_traffic():
     """ncu DRAM bytes per launch of the iteration kernel, if taken on the current kernel source."""
     try:
-        h = hashlib.sha256()
-        for f in KERNEL_SOURCES:
-            h.update(open(f, "rb").read())
-        src = h.hexdigest()
+        src = kernel_source_hash()
         vals = {}
         for line in open(TRAFFIC_FILE):
             if "=" in line and not line.lstrip().startswith("#"):
