@@ -38,13 +38,19 @@ KERNEL_SOURCE = os.path.join(ROOT, "paper_1602_06621_gb300", "csrc", "equilibrat
 KERNEL_HEADER = os.path.join(ROOT, "paper_1602_06621_gb300", "csrc", "sme_internal.cuh")
 
 
+def _section(path, begin, end):
+    text = open(path, "rb").read()
+    a = text.find(begin)
+    b = text.find(end, a + 1) if a >= 0 else -1
+    return text[a:b] if a >= 0 and b > a else text
+
+
 def kernel_source_hash():
+    """Hash of the iteration kernel's device code: its argument structs, tables, accumulators and the kernel
+    itself in equilibrate.cu, and the Philox section of the internal header."""
     h = hashlib.sha256()
-    h.update(open(KERNEL_SOURCE, "rb").read())
-    header = open(KERNEL_HEADER, "rb").read()
-    start = header.find(b"Philox4x32-10")
-    end = header.find(b"------ operator", start)
-    h.update(header[start:end] if start >= 0 and end > start else header)
+    h.update(_section(KERNEL_SOURCE, b"struct SellArgs", b"// Load a start state"))
+    h.update(_section(KERNEL_HEADER, b"Philox4x32-10", b"------ operator"))
     return h.hexdigest()
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sgd_iteration_f32_k32_large.txt")
 # Random 8-byte gathers per second from L2-resident tables, measured on GB300 by

@@ -233,6 +233,8 @@ typedef struct {
     int64_t max_iters;   /* iteration cap */
     int32_t check_every; /* true residual (FP64) checked every this many iterations (>= 1) */
     int32_t stop_rule;   /* 0: ||A x - b|| / ||b||;  1: ||A^T r|| / (||A||_F ||r||) (least squares) */
+    double *history;     /* HOST, may be NULL: the selected residual at every check, in order (sme_lsqr only) */
+    int64_t history_cap; /* entries history can hold */
 } sme_lsqr_params;
 
 typedef struct {
@@ -241,6 +243,7 @@ typedef struct {
     double normal_residual;   /* ||A^T (A x - b)|| / (||A||_F ||A x - b||), FP64 */
     int32_t converged;
     int64_t kernel_launches;  /* device kernels this call launched */
+    int64_t history_count;    /* entries written to p->history */
 } sme_lsqr_result;
 
 /*
@@ -261,10 +264,13 @@ sme_status sme_lsqr(sme_op op, const void *u_bar, const void *v_bar, const void 
 /*
  * A batch of sparse matrices equilibrated together (Algorithm 1 run on each matrix, all matrices
  * advanced by the same launches).  The batch is one block-diagonal operator diag(A_0, ..., A_{B-1})
- * whose rows and columns are sorted by length across the whole batch, so matrices of very different
- * sizes share the same work units.  Matrix b draws its probes from Philox streams stream_base + 2b (s)
+ * laid out matrix by matrix (each matrix's rows and columns sorted by length), so one launch serves
+ * matrices of very different sizes.  Matrix b draws its probes from Philox streams stream_base + 2b (s)
  * and stream_base + 2b + 1 (w) with counters indexed inside matrix b, so its result equals a separate
- * sme_equilibrate of A_b with stream_base + 2b, bit for bit.
+ * sme_equilibrate of A_b with stream_base + 2b (bit for bit when both share slices among the same number
+ * of warps, which is always the case for rows and columns under 48 nonzeros on average).
+ * SME_BATCH_GROUP_BYTES (environment) > 0 lays out groups of consecutive matrices whose gather tables fit
+ * that many bytes instead of single matrices.
  */
 typedef struct sme_batch_s *sme_batch;
 

@@ -6,7 +6,10 @@
 #include <cstdio>
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -30,10 +33,32 @@ sme_status cuda_fail(cudaError_t e, const char *what, int line)
     return e == cudaErrorMemoryAllocation ? SME_ERR_OOM : SME_ERR_CUDA;
 }
 
+// Failure injection for tests: with SME_FAIL_DEV_ALLOC=N in the environment, the (N+1)-th operator allocation
+// after the variable was set (or changed) fails as if the device were out of memory.
+static bool injected_alloc_failure()
+{
+    static std::mutex mu;
+    static std::string armed;
+    static long long calls = 0;
+    const char *env = std::getenv("SME_FAIL_DEV_ALLOC");
+    std::lock_guard<std::mutex> lock(mu);
+    const std::string now = env ? env : "";
+    if (now != armed) {
+        armed = now;
+        calls = 0;
+    }
+    if (armed.empty()) return false;
+    return calls++ == std::atoll(armed.c_str());
+}
+
 sme_status dev_alloc(sme_op op, void **p, size_t bytes)
 {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (injected_alloc_failure()) {
+        set_error("device allocation of %zu bytes failed: injected (SME_FAIL_DEV_ALLOC)", bytes);
+        return SME_ERR_OOM;
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -199,6 +224,7 @@ sme_status sme::create_csr_grouped(sme_op *out, int64_t m, int64_t n, int64_t nn
                                    void *stream, const uint32_t *row_group_host, const uint32_t *col_group_host,
                                    int group_bits)
 {
+    NvtxRange range("sme build");
     if (!out) return SME_ERR_ARG;
     *out = nullptr;
     if (m < 1 || n < 1 || nnz < 0 || nnz > 0x7fffffffLL - 64 || m > 0x7fffffffLL || n > 0x7fffffffLL || !row_ptr ||

@@ -47,6 +47,7 @@ extern "C" sme_status sme_batch_create(sme_batch *out, int32_t count, const int6
                                        const int32_t *const *row_ptr, const int32_t *const *col_idx,
                                        const void *const *vals, sme_dtype dtype, void *stream)
 {
+    NvtxRange range("sme batch build");
     if (!out) return SME_ERR_ARG;
     *out = nullptr;
     if (count < 1 || !m || !n || !row_ptr || !col_idx || !vals || (dtype != SME_F32 && dtype != SME_F64)) {
@@ -184,6 +185,7 @@ extern "C" sme_status sme_batch_get_info(sme_batch b, int32_t *count, int64_t *r
 extern "C" sme_status sme_batch_equilibrate(sme_batch b, const sme_equil_params *p, void *u, void *v, void *u_bar,
                                             void *v_bar, void *stream)
 {
+    NvtxRange range("sme batch equilibrate");
     if (!b || !p || !u || !v || !u_bar || !v_bar || p->T < 0 || p->t_begin < 1 || p->t0 < 0) {
         set_error("sme_batch_equilibrate: bad arguments");
         return SME_ERR_ARG;

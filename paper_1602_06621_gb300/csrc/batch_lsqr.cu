@@ -409,6 +409,7 @@ static sme_status batch_lsqr_t(sme_op op, const real *ubar, const real *vbar, co
         res[b].normal_residual = h.normal_res;
         res[b].converged = metric <= p->tol ? 1 : 0;
         res[b].kernel_launches = b == 0 ? launches : 0;
+        res[b].history_count = 0;
         all_conv = all_conv && res[b].converged;
         finite = finite && std::isfinite(h.rel_res);
     }
@@ -430,6 +431,7 @@ using namespace sme;
 extern "C" sme_status sme_batch_lsqr(sme_batch b, const void *u_bar, const void *v_bar, const void *bvec, void *x,
                                      const sme_lsqr_params *p, sme_lsqr_result *results, void *stream)
 {
+    NvtxRange range("sme batch lsqr");
     if (!b || !bvec || !x || !p || !results || p->max_iters < 0 || p->tol < 0 ||
         (p->stop_rule != 0 && p->stop_rule != 1)) {
         set_error("sme_batch_lsqr: bad arguments");

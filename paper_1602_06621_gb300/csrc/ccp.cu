@@ -438,6 +438,7 @@ extern "C" sme_status sme_ccp_lasso(sme_op op, const void *u_bar, const void *v_
                                     const sme_ccp_params *p, sme_ccp_result *res, double *history,
                                     int64_t history_cap, void *stream)
 {
+    NvtxRange range("sme ccp lasso");
     if (!ccp_op_ok(op, "sme_ccp_lasso")) return SME_ERR_ARG;
     if (!b || !x || !p || !res || !(p->lambda > 0.0) || p->max_iters < 0 || history_cap < 0 ||
         (history_cap > 0 && !history)) {

@@ -464,12 +464,11 @@ static sme_status ensure_dense_workspace(sme_op op, int kp)
         SME_TRY(make_map(&D->mapBf[b], D->Bf[b], 2 * kp, D->n, 256));
         SME_TRY(make_map(&D->mapBb[b], D->Bb[b], 2 * kp, D->m, 256));
     }
-    if (!D->x[0]) {
-        SME_TRY(dev_alloc(op, (void **)&D->x[0], D->m * 4));
-        SME_TRY(dev_alloc(op, (void **)&D->xb[0], D->m * 4));
-        SME_TRY(dev_alloc(op, (void **)&D->x[1], D->n * 4));
-        SME_TRY(dev_alloc(op, (void **)&D->xb[1], D->n * 4));
-    }
+    // Each buffer on its own, so that a call after a failed allocation completes the set.
+    if (!D->x[0]) SME_TRY(dev_alloc(op, (void **)&D->x[0], D->m * 4));
+    if (!D->xb[0]) SME_TRY(dev_alloc(op, (void **)&D->xb[0], D->m * 4));
+    if (!D->x[1]) SME_TRY(dev_alloc(op, (void **)&D->x[1], D->n * 4));
+    if (!D->xb[1]) SME_TRY(dev_alloc(op, (void **)&D->xb[1], D->n * 4));
     D->kcap = kp;
     return SME_OK;
 }
@@ -679,6 +678,7 @@ using namespace sme;
 extern "C" sme_status sme_op_create_dense(sme_op *out, int64_t m, int64_t n, const void *A, int64_t lda,
                                           sme_dtype dtype, const float *row_scales, int on_device, void *stream)
 {
+    NvtxRange range("sme dense build");
     if (!out) return SME_ERR_ARG;
     *out = nullptr;
     if (m < 128 || n < 128 || m % 128 || n % 128 || !A || lda < n || m > (1 << 30) || n > (1 << 30)) {

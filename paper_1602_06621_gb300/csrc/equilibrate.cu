@@ -408,12 +408,11 @@ sme_status ensure_equil_workspace(sme_op op, int kw)
 {
     Workspace &W = op->ws;
     const size_t sz = op->dbl ? 8 : 4;
-    if (!W.u) {
-        SME_TRY(dev_alloc(op, &W.u, op->m * sz));
-        SME_TRY(dev_alloc(op, &W.ub, op->m * sz));
-        SME_TRY(dev_alloc(op, &W.v, op->n * sz));
-        SME_TRY(dev_alloc(op, &W.vb, op->n * sz));
-    }
+    // Each buffer on its own, so that a call after a failed allocation completes the set.
+    if (!W.u) SME_TRY(dev_alloc(op, &W.u, op->m * sz));
+    if (!W.ub) SME_TRY(dev_alloc(op, &W.ub, op->m * sz));
+    if (!W.v) SME_TRY(dev_alloc(op, &W.v, op->n * sz));
+    if (!W.vb) SME_TRY(dev_alloc(op, &W.vb, op->n * sz));
     const int64_t eb = entry_bytes(op->dbl, kw);
     const int64_t need_u = op->fwd.nslices * 32 * eb, need_v = op->bwd.nslices * 32 * eb;
     if (W.tab_bytes_u < need_u) {
@@ -969,6 +968,7 @@ extern "C" sme_status sme_draw_probes(uint64_t seed, int32_t t, int32_t stream_i
 extern "C" sme_status sme_equilibrate(sme_op op, const sme_equil_params *p, void *u, void *v, void *u_bar,
                                       void *v_bar, void *stream)
 {
+    NvtxRange range("sme equilibrate");
     if (!op || !p || !u || !v || !u_bar || !v_bar || p->T < 0 || p->t_begin < 1 || p->t0 < 0) {
         set_error("sme_equilibrate: bad arguments");
         return SME_ERR_ARG;
@@ -1082,6 +1082,7 @@ extern "C" sme_status sme_equilibrate_block(sme_op op, const sme_equil_params *p
 extern "C" sme_status sme_op_autotune(sme_op op, int32_t k, int32_t *slices_per_cta, int32_t *cols_first,
                                       float *ms_per_iteration, void *stream)
 {
+    NvtxRange range("sme autotune");
     if (!op || op->dense) {
         set_error("sme_op_autotune: sparse operators only");
         return SME_ERR_ARG;

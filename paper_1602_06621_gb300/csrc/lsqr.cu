@@ -567,9 +567,19 @@ void release_lsqr(sme_op op)
     op->ws.lsqr = nullptr;
 }
 
+static sme_status alloc_lsqr(sme_op op, cudaStream_t s);
+
+// The op's LSQR state, allocated on first use; a failed allocation leaves no partial state behind.
 static sme_status ensure_lsqr(sme_op op, cudaStream_t s)
 {
     if (lsqr_state(op)) return SME_OK;
+    const sme_status st = alloc_lsqr(op, s);
+    if (st != SME_OK) release_lsqr(op);
+    return st;
+}
+
+static sme_status alloc_lsqr(sme_op op, cudaStream_t s)
+{
     LsqrState *L = new LsqrState();
     op->ws.lsqr = L;
     const size_t sz = op->dbl ? 8 : 4;
@@ -647,7 +657,7 @@ static sme_status lsqr_t(sme_op op, const real *ubar, const real *vbar, const re
     };
     GraphOnce chunk_graph;
     if (p->max_iters >= 2 * (int64_t)every) chunk_graph.capture([&](cudaStream_t q) { enqueue_chunk(every, q); });
-    int64_t it = 0;
+    int64_t it = 0, hcount = 0;
     while (it < p->max_iters) {
         const int64_t chunk = std::min<int64_t>(every, p->max_iters - it);
         if (chunk == every && chunk_graph.exec)
@@ -659,6 +669,9 @@ static sme_status lsqr_t(sme_op op, const real *ubar, const real *vbar, const re
         SME_CUDA(cudaGetLastError());
         SME_CUDA(cudaMemcpyAsync(L->host, L->sc, sizeof(LsqrScalars), cudaMemcpyDeviceToHost, s));
         SME_CUDA(cudaStreamSynchronize(s));
+        if (p->history && hcount < p->history_cap)
+            p->history[hcount] = p->stop_rule == 1 ? L->host->normal_res : L->host->rel_res;
+        ++hcount;
         if (L->host->done) break;
     }
     // Final x in original order, and both residuals of exactly that x.
@@ -676,6 +689,7 @@ static sme_status lsqr_t(sme_op op, const real *ubar, const real *vbar, const re
     const double final_metric = p->stop_rule == 1 ? h.normal_res : h.rel_res;
     res->converged = (h.done != 0 && final_metric <= p->tol) || final_metric <= p->tol ? 1 : 0;
     res->kernel_launches = launches;
+    res->history_count = p->history ? std::min(hcount, p->history_cap) : 0;
     if (!std::isfinite(h.rel_res)) {
         set_error("sme_lsqr: residual became non-finite");
         return SME_ERR_NONFINITE;
@@ -695,6 +709,7 @@ using namespace sme;
 extern "C" sme_status sme_evaluate(sme_op op, const void *u, const void *v, double alpha, double beta, double gamma,
                                    double *r2, double *c2, sme_eval_result *res, void *stream)
 {
+    NvtxRange range("sme evaluate");
     if (!op || !u || !v || !res) {
         set_error("sme_evaluate: bad arguments");
         return SME_ERR_ARG;
@@ -728,7 +743,9 @@ extern "C" sme_status sme_batch_evaluate(sme_batch bt, const void *u, const void
 extern "C" sme_status sme_lsqr(sme_op op, const void *u_bar, const void *v_bar, const void *b, void *x,
                                const sme_lsqr_params *p, sme_lsqr_result *res, void *stream)
 {
-    if (!op || !b || !x || !p || !res || p->max_iters < 0 || p->tol < 0 || (p->stop_rule != 0 && p->stop_rule != 1)) {
+    NvtxRange range("sme lsqr");
+    if (!op || !b || !x || !p || !res || p->max_iters < 0 || p->tol < 0 || (p->stop_rule != 0 && p->stop_rule != 1) ||
+        p->history_cap < 0 || (p->history_cap > 0 && !p->history)) {
         set_error("sme_lsqr: bad arguments");
         return SME_ERR_ARG;
     }

@@ -540,6 +540,7 @@ extern "C" sme_status sme_mlp_gradient(sme_mlp M, const float *X, const float *t
 extern "C" sme_status sme_mlp_train_step(sme_mlp M, const float *X, const float *target, int64_t N, float lr,
                                          float *loss_host, void *stream)
 {
+    NvtxRange range("sme mlp train step");
     SME_TRY(sme_mlp_gradient(M, X, target, N, nullptr, loss_host, stream));
     Mlp &m = M->m;
     m.adam_t += 1;
@@ -564,6 +565,7 @@ extern "C" sme_status sme_op_features(sme_op op, uint64_t seed, float *row_featu
 
 extern "C" sme_status sme_warm_start(sme_op op, sme_mlp M, uint64_t seed, void *u0, void *v0, void *stream)
 {
+    NvtxRange range("sme warm start");
     if (!op || !M || !u0 || !v0 || op->dense) {
         set_error("sme_warm_start: bad arguments");
         return SME_ERR_ARG;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <cstdio>
@@ -59,6 +60,15 @@ struct EventPair {
         cudaError_t r = cudaEventCreate(&e[0]);
         return r == cudaSuccess ? cudaEventCreate(&e[1]) : r;
     }
+};
+
+// An NVTX range around one phase of a call ("sme build", "sme equilibrate", ...), visible to profilers;
+// without a profiler attached the calls are no-ops.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 // Device status word bits (set by kernels, read by sme_op_check).

@@ -74,12 +74,12 @@ class sme_ccp_result(ctypes.Structure):
 
 class sme_lsqr_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int64), ("check_every", ctypes.c_int32),
-                ("stop_rule", ctypes.c_int32)]
+                ("stop_rule", ctypes.c_int32), ("history", ctypes.c_void_p), ("history_cap", ctypes.c_int64)]
 
 
 class sme_lsqr_result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("rel_residual", ctypes.c_double), ("normal_residual", ctypes.c_double),
-                ("converged", ctypes.c_int32), ("kernel_launches", ctypes.c_int64)]
+                ("converged", ctypes.c_int32), ("kernel_launches", ctypes.c_int64), ("history_count", ctypes.c_int64)]
 
 
 _lib = None
@@ -252,14 +252,22 @@ def sme_evaluate(op, u, v, alpha=0.0, beta=0.0, gamma=0.0, r2=None, c2=None, str
 
 
 def sme_lsqr(op, u_bar, v_bar, b, x, *, tol=1e-6, max_iters=100000, check_every=10, stop_rule=0, stream=None,
-             raise_on_not_converged=False) -> dict:
-    p = sme_lsqr_params(float(tol), int(max_iters), int(check_every), int(stop_rule))
+             raise_on_not_converged=False, history=False) -> dict:
+    """LSQR on D A E (Section 5.1).  With history=True the result's "history" lists the checked residual
+    at every check (every check_every iterations)."""
+    cap = (int(max_iters) // max(1, int(check_every)) + 1) if history else 0
+    hist = np.zeros(max(cap, 1))
+    p = sme_lsqr_params(float(tol), int(max_iters), int(check_every), int(stop_rule),
+                        ctypes.c_void_p(hist.ctypes.data) if cap else None, cap)
     res = sme_lsqr_result()
     st = load().sme_lsqr(op, _ptr(u_bar), _ptr(v_bar), _ptr(b), _ptr(x), ctypes.byref(p), ctypes.byref(res),
                          _stream(stream))
     if st != -7 or raise_on_not_converged:
         _check(st, "sme_lsqr")
-    return {f: getattr(res, f) for f, _ in sme_lsqr_result._fields_}
+    out = {f: getattr(res, f) for f, _ in sme_lsqr_result._fields_}
+    if history:
+        out["history"] = list(hist[:res.history_count])
+    return out
 
 
 def sme_estimate_rows_static(m, n, row_ptr, col_idx, vals, u, v, t, k, seed, stream_base, z_u, stream=None):
@@ -339,7 +347,7 @@ def sme_batch_lsqr(b, u_bar, v_bar, bvec, x, *, tol=1e-6, max_iters=100000, chec
                    raise_on_not_converged=False):
     """Per-matrix LSQR over a batch; returns a list of per-matrix result dicts."""
     count = sme_batch_get_info(b)[0]
-    p = sme_lsqr_params(float(tol), int(max_iters), int(check_every), int(stop_rule))
+    p = sme_lsqr_params(float(tol), int(max_iters), int(check_every), int(stop_rule), None, 0)
     res = (sme_lsqr_result * count)()
     st = load().sme_batch_lsqr(b, _ptr(u_bar), _ptr(v_bar), _ptr(bvec), _ptr(x), ctypes.byref(p),
                                ctypes.cast(res, ctypes.c_void_p), _stream(stream))

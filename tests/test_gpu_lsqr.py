@@ -159,3 +159,18 @@ def test_long_rows_iterates_match_oracle_fp64(scaled, iters):
     tol = 1e-9 if iters <= 6 else 1e-7
     assert np.linalg.norm(x - xo) <= tol * np.linalg.norm(xo)
     assert res["rel_residual"] == pytest.approx(_rel_res(A, x, b), rel=1e-9)
+
+
+def test_residual_history_is_the_residual_at_each_check(small):
+    """history[i] is ||A x - b|| / ||b|| of the iterate after (i + 1) * check_every iterations, the same value a
+    run stopped there reports."""
+    A, op, dt = small
+    b = O.csr_matvec(A, I.normal_vector(A.n, 8))
+    _, _, ub, vb = O.equilibrate(A, T=30, k=1, seed=0)
+    _, res = _gpu_lsqr(op, dt, ub, vb, b, A.n, tol=0.0, max_iters=40, check_every=5, history=True)
+    hist = res["history"]
+    assert res["history_count"] == len(hist) == 8
+    for i in (0, 3, 7):
+        _, r_i = _gpu_lsqr(op, dt, ub, vb, b, A.n, tol=0.0, max_iters=5 * (i + 1), check_every=5)
+        assert hist[i] == pytest.approx(r_i["rel_residual"], rel=1e-12)
+    assert hist[-1] == pytest.approx(res["rel_residual"], rel=1e-12)
