@@ -161,6 +161,42 @@ sme_status validate_csr_host(int64_t m, int64_t n, int64_t nnz, const int32_t *r
                             : validate_host<float>(m, n, nnz, rp, col, (const float *)vals);
 }
 
+// A host check running on its own thread; result() waits for it, report() re-raises its message on the
+// calling thread (error messages are per thread).
+class HostValidation {
+  public:
+    template <typename F>
+    void start(F &&check)
+    {
+        running_ = true;
+        worker_ = std::thread([this, check] {
+            status_ = check();
+            if (status_ != SME_OK) message_ = sme_last_error();
+        });
+    }
+    sme_status result()
+    {
+        if (running_) {
+            worker_.join();
+            running_ = false;
+        }
+        return status_;
+    }
+    sme_status report()
+    {
+        const sme_status st = result();
+        set_error("%s", message_.c_str());
+        return st;
+    }
+    ~HostValidation() { result(); }
+
+  private:
+    std::thread worker_;
+    bool running_ = false;
+    sme_status status_ = SME_OK;
+    std::string message_;
+};
+
 }  // namespace sme
 
 using namespace sme;
@@ -237,13 +273,15 @@ sme_status sme::create_csr_grouped(sme_op *out, int64_t m, int64_t n, int64_t nn
         return SME_ERR_ARG;
     }
     const size_t vsz = dtype == SME_F64 ? 8 : 4;
-    if (!on_device) {
-        sme_status st = dtype == SME_F64
-                            ? validate_host<double>(m, n, nnz, row_ptr, col_idx, (const double *)vals)
-                            : validate_host<float>(m, n, nnz, row_ptr, col_idx, (const float *)vals);
-        if (st != SME_OK) return st;
-    }
     cudaStream_t s = (cudaStream_t)stream;
+    // Host input is checked on a host thread while the device is set up; its verdict is taken before
+    // anything is built, and an invalid input is reported as such even when the device setup fails too.
+    HostValidation validation;
+    if (!on_device)
+        validation.start([=] {
+            return dtype == SME_F64 ? validate_host<double>(m, n, nnz, row_ptr, col_idx, (const double *)vals)
+                                    : validate_host<float>(m, n, nnz, row_ptr, col_idx, (const float *)vals);
+        });
     sme_op op = new sme_op_s();
     op->m = m;
     op->n = n;
@@ -253,7 +291,7 @@ sme_status sme::create_csr_grouped(sme_op *out, int64_t m, int64_t n, int64_t nn
     sme_status st = dev_alloc(op, (void **)&op->d_status, sizeof(int));
     if (st != SME_OK) {
         sme_op_destroy(op);
-        return st;
+        return validation.result() != SME_OK ? validation.report() : st;
     }
     const int32_t *d_rp = row_ptr, *d_col = col_idx;
     const void *d_val = vals;
@@ -268,6 +306,7 @@ sme_status sme::create_csr_grouped(sme_op *out, int64_t m, int64_t n, int64_t nn
                 for (void *p : tmp)
                     if (p) cudaFree(p);
                 sme_op_destroy(op);
+                if (validation.result() != SME_OK) return validation.report();
                 set_error("sme_op_create_csr: staging allocation failed");
                 return SME_ERR_OOM;
             }
@@ -277,6 +316,14 @@ sme_status sme::create_csr_grouped(sme_op *out, int64_t m, int64_t n, int64_t nn
         d_rp = (const int32_t *)tmp[0];
         d_col = (const int32_t *)tmp[1];
         d_val = tmp[2];
+        // The copies are in flight (overlapping the host check when the input is pinned).
+        if (validation.result() != SME_OK) {
+            cudaStreamSynchronize(s);
+            for (void *p : tmp)
+                if (p) cudaFree(p);
+            sme_op_destroy(op);
+            return validation.report();
+        }
     }
     uint32_t *groups[2] = {nullptr, nullptr};
     if (row_group_host && col_group_host) {

@@ -269,7 +269,7 @@ static void bl_release(BLsqr *L)
                     (void *)L->sq_r2, (void *)L->r, (void *)L->roff, (void *)L->coff, (void *)L->sc,
                     (void *)L->list_r, (void *)L->list_c})
         if (p) cudaFree(p);
-    if (L->host) cudaFreeHost(L->host);
+    delete[] L->host;
     delete L;
 }
 
@@ -293,11 +293,11 @@ static sme_status batch_lsqr_t(sme_op op, const real *ubar, const real *vbar, co
     if (cudaMalloc(&L->sq_r, M * 8) != cudaSuccess || cudaMalloc(&L->sq_r2, M * 8) != cudaSuccess ||
         cudaMalloc(&L->r, M * 8) != cudaSuccess || cudaMalloc(&L->sq_c, N * 8) != cudaSuccess ||
         cudaMalloc(&L->roff, (count + 1) * 8) != cudaSuccess || cudaMalloc(&L->coff, (count + 1) * 8) != cudaSuccess ||
-        cudaMalloc(&L->sc, count * sizeof(BScal)) != cudaSuccess ||
-        cudaMallocHost(&L->host, count * sizeof(BScal)) != cudaSuccess) {
+        cudaMalloc(&L->sc, count * sizeof(BScal)) != cudaSuccess) {
         cudaGetLastError();
         return fail(SME_ERR_OOM);
     }
+    L->host = new BScal[count]();
     const Sell &F = op->fwd, &Bk = op->bwd;
     const int32_t *mid_r = B->mid[0], *mid_c = B->mid[1];
     real *ud = (real *)L->ud, *ve = (real *)L->ve, *w = (real *)L->w, *x = (real *)L->x, *d = (real *)L->d,

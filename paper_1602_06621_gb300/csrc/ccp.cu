@@ -233,7 +233,7 @@ static void ccp_release(CcpState *C)
     for (void *p : {C->d, C->e, C->bs, C->y, C->yd, C->xs, C->xe, C->xt, (void *)C->partials, (void *)C->counter,
                     (void *)C->sc})
         if (p) cudaFree(p);
-    if (C->host) cudaFreeHost(C->host);
+    delete C->host;
     delete C;
 }
 
@@ -250,11 +250,11 @@ static sme_status ccp_alloc(sme_op op, CcpState *C, size_t sz)
     for (int i = 0; nv[i]; ++i) ok = ok && cudaMalloc(nv[i], (size_t)n * sz) == cudaSuccess;
     if (!ok ||cudaMalloc(&C->partials, (size_t)maxb * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&C->counter, sizeof(unsigned)) != cudaSuccess ||
-        cudaMalloc(&C->sc, sizeof(CcpScalars)) != cudaSuccess ||
-        cudaMallocHost(&C->host, sizeof(CcpScalars)) != cudaSuccess) {
+        cudaMalloc(&C->sc, sizeof(CcpScalars)) != cudaSuccess) {
         cudaGetLastError();
         return SME_ERR_OOM;
     }
+    C->host = new CcpScalars();
     return SME_OK;
 }
 

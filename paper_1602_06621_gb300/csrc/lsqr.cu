@@ -312,7 +312,7 @@ struct LsqrState {
     double *partials;  // 2 * max blocks
     unsigned *counter;
     LsqrScalars *sc;
-    LsqrScalars *host;  // pinned mirror
+    LsqrScalars *host;  // host mirror
     int64_t bytes;
     int64_t fwd_blocks, bwd_blocks;
     double afro;  // cached ||A||_F (< 0: not computed)
@@ -562,7 +562,7 @@ void release_lsqr(sme_op op)
     for (void *p : {L->ud, L->ve, L->w, L->x, L->d, L->e, L->bs, L->xt, (void *)L->r, (void *)L->partials,
                     (void *)L->counter, (void *)L->sc})
         if (p) cudaFree(p);
-    if (L->host) cudaFreeHost(L->host);
+    delete L->host;
     delete L;
     op->ws.lsqr = nullptr;
 }
@@ -600,7 +600,7 @@ static sme_status alloc_lsqr(sme_op op, cudaStream_t s)
     SME_TRY(dev_alloc(op, (void **)&L->partials, 2 * maxb * sizeof(double)));
     SME_TRY(dev_alloc(op, (void **)&L->counter, sizeof(unsigned)));
     SME_TRY(dev_alloc(op, (void **)&L->sc, sizeof(LsqrScalars)));
-    SME_CUDA(cudaMallocHost((void **)&L->host, sizeof(LsqrScalars)));
+    L->host = new LsqrScalars();  // a one-struct mirror: pageable memory is as fast as pinned here
     SME_CUDA(cudaMemsetAsync(L->counter, 0, sizeof(unsigned), s));
     L->afro = -1.0;
     return SME_OK;
