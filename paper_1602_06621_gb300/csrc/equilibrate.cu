@@ -671,23 +671,33 @@ static sme_status equilibrate_t(sme_op op, const sme_equil_params *p, real *u, r
                                  (int64_t)(R.alpha * 1e15), (int64_t)(R.beta * 1e15), (int64_t)(R.gamma * 1e15),
                                  (int64_t)(R.M * 1e15), (int64_t)op->ws.tab_bytes_u,
                                  sh.spc * 4 + sh.cols_first * 2 + (op->ws.use_tgt ? 1 : 0)};
+        // A call is captured only when it repeats the previous one: a one-off call (a fresh operator, new
+        // parameters) launches directly and does not pay for capture and instantiation.
         GraphCache &G = op->graph;
-        if (!G.exec || std::memcmp(G.key, key, sizeof(key)) != 0) {
-            if (G.exec) {
-                cudaGraphExecDestroy(G.exec);
-                G.exec = nullptr;
+        const bool cached = G.exec && std::memcmp(G.key, key, sizeof(key)) == 0;
+        const bool repeat = !cached && G.have_direct && std::memcmp(G.last_direct, key, sizeof(key)) == 0;
+        if (!cached && !repeat) {
+            enqueue(s);
+            std::memcpy(G.last_direct, key, sizeof(key));
+            G.have_direct = true;
+        } else {
+            if (!cached) {
+                if (G.exec) {
+                    cudaGraphExecDestroy(G.exec);
+                    G.exec = nullptr;
+                }
+                if (!G.stream) SME_CUDA(cudaStreamCreateWithFlags(&G.stream, cudaStreamNonBlocking));
+                cudaGraph_t graph = nullptr;
+                SME_CUDA(cudaStreamBeginCapture(G.stream, cudaStreamCaptureModeThreadLocal));
+                enqueue(G.stream);
+                SME_CUDA(cudaStreamEndCapture(G.stream, &graph));
+                cudaError_t e = cudaGraphInstantiate(&G.exec, graph, 0);
+                cudaGraphDestroy(graph);
+                SME_CUDA(e);
+                std::memcpy(G.key, key, sizeof(key));
             }
-            if (!G.stream) SME_CUDA(cudaStreamCreateWithFlags(&G.stream, cudaStreamNonBlocking));
-            cudaGraph_t graph = nullptr;
-            SME_CUDA(cudaStreamBeginCapture(G.stream, cudaStreamCaptureModeThreadLocal));
-            enqueue(G.stream);
-            SME_CUDA(cudaStreamEndCapture(G.stream, &graph));
-            cudaError_t e = cudaGraphInstantiate(&G.exec, graph, 0);
-            cudaGraphDestroy(graph);
-            SME_CUDA(e);
-            std::memcpy(G.key, key, sizeof(key));
+            SME_CUDA(cudaGraphLaunch(G.exec, s));
         }
-        SME_CUDA(cudaGraphLaunch(G.exec, s));
     }
     if (timed) {
         SME_CUDA(cudaEventRecord(op->ev_loop[1], s));

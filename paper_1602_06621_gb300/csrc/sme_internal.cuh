@@ -163,7 +163,9 @@ struct Workspace {
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     cudaStream_t stream = nullptr;
-    int64_t key[12] = {0};
+    int64_t key[12] = {0};       // parameters of the captured graph
+    int64_t last_direct[12] = {0};  // parameters of the last call launched directly
+    bool have_direct = false;
 };
 
 struct DenseOp;  // tensor-core operator (dense A)

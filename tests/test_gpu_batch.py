@@ -100,15 +100,17 @@ def test_graph_replay_equals_direct_launches():
     A = I.workload_large(scale=0.004, seed=4)
     op, dt = make_op(A)
     try:
-        g1 = gpu_equilibrate(op, dt, A.m, A.n, T=30, k=32, seed=1)
-        g2 = gpu_equilibrate(op, dt, A.m, A.n, T=30, k=32, seed=1)  # replays the cached graph
+        g1 = gpu_equilibrate(op, dt, A.m, A.n, T=30, k=32, seed=1)  # first call: direct launches
+        g2 = gpu_equilibrate(op, dt, A.m, A.n, T=30, k=32, seed=1)  # repeated: captured and launched
+        g2b = gpu_equilibrate(op, dt, A.m, A.n, T=30, k=32, seed=1)  # replays the cached graph
         d1 = gpu_equilibrate(op, dt, A.m, A.n, T=30, k=32, seed=1, flags=sme.SME_EQ_NO_GRAPH)
         g3 = gpu_equilibrate(op, dt, A.m, A.n, T=30, k=32, seed=2)  # new key: captured again
         d3 = gpu_equilibrate(op, dt, A.m, A.n, T=30, k=32, seed=2, flags=sme.SME_EQ_NO_GRAPH)
     finally:
         sme.sme_op_destroy(op)
-    for a, b_, c in zip(g1, g2, d1):
+    for a, b_, bb, c in zip(g1, g2, g2b, d1):
         np.testing.assert_array_equal(a, b_)
+        np.testing.assert_array_equal(a, bb)
         np.testing.assert_array_equal(a, c)
     for a, c in zip(g3, d3):
         np.testing.assert_array_equal(a, c)
