@@ -5,17 +5,24 @@
 // so each B operand holds two BF16 terms: B = [hi | lo] with hi = bf16(x), lo = bf16(x - hi), and the
 // two accumulators are added in the epilogue (relative error of the scaling ~2^-17 instead of 2^-9).
 //
-// Both products are the same GEMM, X (M x K, row-major BF16) times B^T (N x K, row-major BF16):
-// the op keeps A and a transposed copy A^T, so every operand is K-major.  One launch performs one
-// iteration: CTAs [0, m/128) take 128-row tiles of A (forward), the others 128-row tiles of A^T.
-// Each CTA owns its full output tile (128 x 2k FP32 in TMEM, 2k <= 512 columns), streams K through a
-// 5-to-8-stage TMA pipeline (64-byte swizzle), one thread issues tcgen05.mma, and four epilogue warps
-// read TMEM and finish the row in registers: z = e^{2x} (1/k) sum_p (hi_p + lo_p)^2, the projected
-// step, the running average, and the row's slice of the NEXT iteration's B operand (its scale and
-// Philox probe bits), double-buffered like the sparse path's gather tables.
+// Both products are the same GEMM, X (M x K, BF16) times B^T (N x K, row-major BF16): the op keeps A
+// and a transposed copy A^T, so every operand is K-major, both stored K-blocked (each 128 x 64 tile one
+// contiguous 16 KB run).  One launch performs one iteration: the first CTAs take tiles of A (forward),
+// the others tiles of A^T.  CTAs run in clusters of two, one per SM of a pair, on 256 rows of one
+// product: the leader issues M = 256 tcgen05.mma (cta_group::2), each CTA holding its 128 rows of X and
+// one half of every 256-row operand unit, and each CTA's TMEM receiving its 128 rows x 2k FP32
+// (2k <= 512 columns).  K streams in blocks of 64 through two rings of shared-memory slots filled by TMA
+// (128-byte swizzle), one for X, one for the operand halves, each slot released in both CTAs as soon as
+// its own MMAs complete.  The producer and MMA-issue loops are kept to a few instructions per slot: the
+// issuing thread runs only slightly ahead of the tensor core, so anything more on that path shows up
+// directly as idle tensor cycles.  Four epilogue warps per CTA read TMEM and finish each row in
+// registers: z = e^{2x} (1/k) sum_p (hi_p + lo_p)^2, the projected step, the running average, and the
+// row's slice of the NEXT iteration's B operand (its scale and Philox probe bits), double-buffered like
+// the sparse path's gather tables.
 //
-// Every wait on an mbarrier is bounded: on expiry the kernel sets ST_TIMEOUT in the op's status word,
-// waits (bounded) for its own outstanding copies and MMAs, frees its TMEM and returns.
+// Every wait on an mbarrier is bounded: on expiry the kernel sets ST_TIMEOUT in the op's status word
+// (the epilogue then writes nothing), waits (bounded) for the MMAs in flight, frees its TMEM, and leaves
+// after a cluster barrier that keeps both CTAs resident until neither can still be written to.
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -28,27 +35,33 @@
 
 namespace sme {
 
-constexpr int DN_BM = 128;           // rows per tile (MMA M)
-constexpr int DN_BK = 32;            // K per stage: 32 BF16 = one 64-byte swizzle row
-constexpr int DN_ROWB = DN_BK * 2;   // bytes per operand row in shared memory
-constexpr int DN_SMEM_BUDGET = 200 * 1024;
+constexpr int DN_BM = 128;                  // rows per CTA (the pair's MMA has M = 256)
+constexpr int DN_BK = 64;                   // K per block: 64 BF16 = one 128-byte swizzle row
+constexpr int DN_ROWB = DN_BK * 2;          // bytes per operand row in shared memory
+constexpr int DN_A_SLOT = DN_BM * DN_ROWB;  // 16 KB: one K-block of this CTA's 128 rows of A (or A^T)
+constexpr int DN_B_SLOT = 128 * DN_ROWB;    // 16 KB: one K-block of this CTA's half of a 256-row operand unit
 
-// Pipeline depth: as many stages as fit the shared-memory budget (5 for k = 256, 8 for k = 128).
+// Ring depths: four K-blocks in flight (k = 256: one A slot and two operand halves, hi and lo, per
+// K-block; k = 128: hi and lo together are one 256-row unit).
 template <int KP>
 struct DenseCfg {
     static constexpr int NT = 2 * KP;
-    static constexpr int A_BYTES = DN_BM * DN_ROWB;
-    static constexpr int B_BYTES = NT * DN_ROWB;
-    static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int STAGES = (DN_SMEM_BUDGET / STAGE) > 8 ? 8 : (DN_SMEM_BUDGET / STAGE);
+    static constexpr int UNITS = NT / 256;  // operand units (one MMA's N = 256) per K-block
+    static constexpr int A_SLOTS = KP == 256 ? 4 : 6;
+    static constexpr int B_SLOTS = KP == 256 ? 8 : 6;
+    static constexpr int BYTES = A_SLOTS * DN_A_SLOT + B_SLOTS * DN_B_SLOT;
 };
+static_assert(DenseCfg<256>::BYTES + 1024 <= 227 * 1024 && DenseCfg<128>::BYTES + 1024 <= 227 * 1024,
+              "dense rings exceed the shared memory of one CTA");
 constexpr int DN_THREADS = 192;      // warp 0 TMA, warp 1 MMA + TMEM owner, warps 2..5 epilogue
 constexpr uint32_t DN_WAIT_LIMIT = 1u << 22;  // polls of a try_wait before a wait is abandoned
 
 struct DenseOp {
     bool fp8 = false;
     int64_t m = 0, n = 0;
-    __nv_bfloat16 *A = nullptr, *At = nullptr;  // row-major m x n and n x m
+    // A (m x n) and A^T (n x m) in K-blocked order: the 128 x 64 block (row tile t, K-block kb) is one
+    // contiguous 16 KB run at ((t * cols/64 + kb) * 128) * 64 elements, rows of 64 inside it.
+    __nv_bfloat16 *A = nullptr, *At = nullptr;
     float *row_scale = nullptr;                 // FP8 input: per-row scales (applied in the epilogue)
     __nv_bfloat16 *Bf[2] = {nullptr, nullptr};  // [2k][n]: forward operand (columns' scale x probes)
     __nv_bfloat16 *Bb[2] = {nullptr, nullptr};  // [2k][m]: backward operand
@@ -93,25 +106,48 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
     return false;
 }
 
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+// Shared-memory address, in the cluster window, of the same variable in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+
+// Copy into this CTA's shared memory whose completion is counted on an mbarrier of either CTA of the
+// pair (`bar_cluster`: a cluster-window address).
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, int x, int y, uint32_t bar_cluster)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar_cluster)
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row groups 512 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc_sw64(const void *p)
+__device__ __forceinline__ uint32_t cluster_rank()
 {
-    const uint64_t addr = smem_u32(p);
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// All threads of every CTA of the cluster.
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128_u32(uint32_t saddr)
+{
+    const uint64_t addr = saddr;
     uint64_t d = 0;
     d |= (addr >> 4) & 0x3FFFull;              // start address
     d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)((8 * DN_ROWB) >> 4) << 32; // stride byte offset: 8 rows x 64 bytes
+    d |= (uint64_t)((8 * DN_ROWB) >> 4) << 32; // stride byte offset: 8 rows x 128 bytes
     d |= (uint64_t)1 << 46;                    // descriptor version for tcgen05
-    d |= (uint64_t)4 << 61;                    // swizzle mode: 64 bytes
+    d |= (uint64_t)2 << 61;                    // swizzle mode: 128 bytes
     return d;
 }
 
@@ -127,13 +163,16 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t *bar)
+// Arrives on the mbarrier at `bar`'s offset in every CTA of `mask` once this thread's MMAs have completed.
+__device__ __forceinline__ void mma_commit_multicast(uint64_t *bar, uint16_t mask)
 {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                     smem_u32(bar)),
+                 "h"(mask)
                  : "memory");
 }
 
@@ -157,7 +196,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
 
 struct DenseArgs {
     int64_t m, n;
-    int row_tiles;            // m / 128; CTAs beyond are column tiles
+    int row_tiles, col_tiles; // m / 128, n / 128
+    int row_ctas;             // CTAs of the forward product: row_tiles rounded up to whole clusters
     int kp;                   // probes (128 or 256)
     float *x[2], *xb[2];      // [0] u, ubar (rows)   [1] v, vbar (columns)
     float *z[2];              // estimate-only outputs, or null
@@ -179,92 +219,117 @@ template <int KP>
 __global__ void __launch_bounds__(DN_THREADS, 1) dense_iteration(const __grid_constant__ DenseMaps maps, DenseArgs a)
 {
     using C = DenseCfg<KP>;
-    constexpr int NT = C::NT;                        // accumulator columns: hi then lo
-    constexpr int A_BYTES = C::A_BYTES;
-    constexpr int STAGE = C::STAGE;
-    constexpr int DN_STAGES = C::STAGES;
-    constexpr uint32_t IDESC = idesc_bf16(DN_BM, 256);
+    constexpr int NT = C::NT;  // accumulator columns: hi then lo
+    constexpr int UNITS = C::UNITS, NA = C::A_SLOTS, NB = C::B_SLOTS;
+    constexpr uint32_t IDESC = idesc_bf16(2 * DN_BM, 256);
+    constexpr uint16_t PAIR = 0x3;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t full_bar[8], empty_bar[8], acc_bar;
+    uint8_t *ring_a = smem;                    // NA slots of DN_A_SLOT bytes
+    uint8_t *ring_b = smem + NA * DN_A_SLOT;   // NB slots of DN_B_SLOT bytes
+    // The full barriers of the leader (rank 0) count both CTAs' copies; the empty barriers of each CTA and
+    // its acc_bar are signalled by the leader's MMA commits.
+    __shared__ uint64_t a_full[NA], a_empty[NA], b_full[NB], b_empty[NB], acc_bar;
     __shared__ uint32_t tmem_base_sh;
-    __shared__ int abort_sh, issued_sh, consumed_sh;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool cols = (int)blockIdx.x >= a.row_tiles;
-    const int tile = cols ? (int)blockIdx.x - a.row_tiles : (int)blockIdx.x;
+    // A cluster of two CTAs (one per SM of a pair) computes 256 rows of one product with M = 256 MMAs
+    // (cta_group::2): each CTA holds its 128 rows of A and one half of every 256-row operand unit, the
+    // leader issues the MMAs, and each CTA's TMEM receives its own rows.  With an odd tile count the
+    // second CTA of the last cluster repeats its partner's rows and writes nothing.
+    const bool cols = (int)blockIdx.x >= a.row_ctas;
+    const int idx = cols ? (int)blockIdx.x - a.row_ctas : (int)blockIdx.x;
+    const int ntiles = cols ? a.col_tiles : a.row_tiles;
+    const bool active = idx < ntiles;
+    const int tile = active ? idx : ntiles - 1;
+    const uint32_t crank = cluster_rank();
+    const bool leader = crank == 0;
     const int64_t K = cols ? a.m : a.n;              // reduction length
     const int nk = (int)(K / DN_BK);
     const CUtensorMap *mapX = cols ? &maps.X[1] : &maps.X[0];
     const CUtensorMap *mapB = cols ? &maps.B[1] : &maps.B[0];
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < DN_STAGES; ++s) {
-            mbar_init(&full_bar[s], 1);
-            mbar_init(&empty_bar[s], 1);
+        for (int s = 0; s < NA; ++s) {
+            mbar_init(&a_full[s], 1);
+            mbar_init(&a_empty[s], 1);
+        }
+        for (int s = 0; s < NB; ++s) {
+            mbar_init(&b_full[s], 1);
+            mbar_init(&b_empty[s], 1);
         }
         mbar_init(&acc_bar, 1);
-        abort_sh = 0;
-        issued_sh = 0;
-        consumed_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+    if (warp == 1) {  // one warp of each CTA of the pair allocates, collectively
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
                      "r"((uint32_t)NT));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
+    cluster_sync();  // both CTAs' barriers are initialised before the pair signals them
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_sh;
 
-    int issued_mma = 0;  // MMA issuer: stages whose MMAs were issued
     if (warp == 0 && lane == 0) {
-        // TMA producer.
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % DN_STAGES;
-            if (kb >= DN_STAGES && !mbar_wait(&empty_bar[s], ((kb / DN_STAGES) - 1) & 1)) {
-                atomicOr(a.status, ST_TIMEOUT);
-                atomicExch(&abort_sh, 1);
+        // TMA producer (both CTAs): for each K-block this CTA's A slot, then its halves of the operand units,
+        // in the order the leader consumes them; completion is counted on the leader's full barriers.  The
+        // loop is kept minimal: the MMA issuer runs only a few instructions ahead of the tensor core.
+        bool bad = false;
+        for (int kb = 0; kb < nk && !bad; ++kb) {
+            const int sa = kb % NA;
+            if (kb >= NA && !mbar_wait(&a_empty[sa], ((kb / NA) - 1) & 1)) {
+                bad = true;
                 break;
             }
-            if (*(volatile int *)&abort_sh) break;
-            uint8_t *sa = smem + s * STAGE;
-            uint8_t *sb = sa + A_BYTES;
-            mbar_expect_tx(&full_bar[s], STAGE);
-            tma_load_2d(sa, mapX, kb * DN_BK, tile * DN_BM, &full_bar[s]);
-            for (int h = 0; h < NT / 256; ++h)
-                tma_load_2d(sb + h * 256 * DN_ROWB, mapB, kb * DN_BK, h * 256, &full_bar[s]);
-            issued_sh = kb + 1;
-        }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer.
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % DN_STAGES;
-            if (!mbar_wait(&full_bar[s], (kb / DN_STAGES) & 1)) {
-                atomicOr(a.status, ST_TIMEOUT);
-                atomicExch(&abort_sh, 1);
-                break;
-            }
-            if (*(volatile int *)&abort_sh) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            uint8_t *sa = smem + s * STAGE;
-            uint8_t *sb = sa + A_BYTES;
-#pragma unroll
-            for (int kk = 0; kk < DN_BK / 16; ++kk) {
-                const uint64_t ad = smem_desc_sw64(sa) + (uint64_t)(kk * 2);  // +32 bytes along K
-#pragma unroll
-                for (int h = 0; h < NT / 256; ++h) {
-                    const uint64_t bd = smem_desc_sw64(sb + h * 256 * DN_ROWB) + (uint64_t)(kk * 2);
-                    mma_bf16(tmem + h * 256, ad, bd, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
+            if (leader) mbar_expect_tx(&a_full[sa], 2 * DN_A_SLOT);
+            tma_load_2d_pair(ring_a + sa * DN_A_SLOT, mapX, 0, (tile * nk + kb) * DN_BM, cluster_addr(&a_full[sa], 0));
+            for (int j = 0; j < UNITS; ++j) {
+                const int q = kb * UNITS + j, sb = q % NB;
+                if (q >= NB && !mbar_wait(&b_empty[sb], ((q / NB) - 1) & 1)) {
+                    bad = true;
+                    break;
                 }
+                if (leader) mbar_expect_tx(&b_full[sb], 2 * DN_B_SLOT);
+                tma_load_2d_pair(ring_b + sb * DN_B_SLOT, mapB, kb * DN_BK, j * 256 + (int)crank * 128,
+                                 cluster_addr(&b_full[sb], 0));
             }
-            mma_commit(&empty_bar[s]);
-            ++issued_mma;
-            consumed_sh = kb + 1;
         }
-        mma_commit(&acc_bar);  // arrives once every MMA issued above has completed
+        if (bad) atomicOr(a.status, ST_TIMEOUT);
+    } else if (warp == 1 && lane == 0 && leader) {
+        // MMA issuer (leader only): four K=16 MMAs (M = 256 over the pair, N = 256) per operand unit into
+        // that unit's 256 accumulator columns; each slot is released in both CTAs as soon as its MMAs
+        // complete, the A slot after the block's last unit.
+        const uint32_t sbase = smem_u32(smem);
+        bool bad = false;
+        for (int kb = 0; kb < nk && !bad; ++kb) {
+            const int sa = kb % NA;
+            if (!mbar_wait(&a_full[sa], (kb / NA) & 1)) {
+                bad = true;
+                break;
+            }
+            const uint64_t ad0 = smem_desc_sw128_u32(sbase + (uint32_t)(sa * DN_A_SLOT));
+            for (int j = 0; j < UNITS; ++j) {
+                const int q = kb * UNITS + j, sb = q % NB;
+                if (!mbar_wait(&b_full[sb], (q / NB) & 1)) {
+                    bad = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t bd0 = smem_desc_sw128_u32(sbase + (uint32_t)(NA * DN_A_SLOT + sb * DN_B_SLOT));
+#pragma unroll
+                for (int kk = 0; kk < DN_BK / 16; ++kk)  // +32 bytes along K per step
+                    mma_bf16(tmem + j * 256, ad0 + (uint64_t)(kk * 2), bd0 + (uint64_t)(kk * 2), IDESC,
+                             (kb > 0 || kk > 0) ? 1u : 0u);
+                mma_commit_multicast(&b_empty[sb], PAIR);
+            }
+            if (!bad) mma_commit_multicast(&a_empty[sa], PAIR);
+        }
+        if (bad) {
+            atomicOr(a.status, ST_TIMEOUT);  // seen by the epilogue, which then writes nothing
+            __threadfence();
+        }
+        mma_commit_multicast(&acc_bar, PAIR);  // arrives in both CTAs once every MMA above has completed
     }
 
     // Epilogue: warps 2..5, one TMEM lane (one row of the tile) per thread.
@@ -289,7 +354,7 @@ __global__ void __launch_bounds__(DN_THREADS, 1) dense_iteration(const __grid_co
             }
         }
         const int side = cols ? 1 : 0;
-        if (ok && !*(volatile int *)&abort_sh) {
+        if (ok && active && !(*(volatile int *)a.status & ST_TIMEOUT)) {
             float *X = a.x[side];
             const float xo = X[r];
             const float ex = expf(xo);
@@ -328,18 +393,19 @@ __global__ void __launch_bounds__(DN_THREADS, 1) dense_iteration(const __grid_co
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        // After an abandoned wait: let copies that were issued but never consumed land before exiting.
-        for (int kb = consumed_sh; kb < issued_sh; ++kb) mbar_wait(&full_bar[kb % DN_STAGES], (kb / DN_STAGES) & 1);
-    }
     if (warp == 1) {
         // MMAs still in flight must finish before their TMEM is released (bounded; completes at once normally).
         if (lane == 0) mbar_wait(&acc_bar, 0);
         __syncwarp();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)NT));
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)NT));
     }
-    (void)issued_mma;
+    // Neither CTA leaves while copies or commits of the pair may still target its shared memory.  After an
+    // abandoned wait anywhere (the status bit is set before the CTA that gave up reaches this barrier),
+    // copies already issued are given time to land.
+    cluster_sync();
+    if (threadIdx.x == 0 && (*(volatile int *)a.status & ST_TIMEOUT))
+        for (int i = 0; i < 2000; ++i) __nanosleep(1000);
 }
 
 // Operand of iteration t from a state vector: B[p][i] = s_ip * hi(e^{x_i}), B[k+p][i] = s_ip * lo(e^{x_i}).
@@ -361,6 +427,21 @@ __global__ void dense_build_operand(int64_t len, int kp, const float *x, const f
             B[(int64_t)(kp + pp) * len + i] = neg ? __hneg(lo) : lo;
         }
     }
+}
+
+// Element offset of (i, j) in the K-blocked order of a rows x cols matrix (cols a multiple of 64).
+__host__ __device__ __forceinline__ int64_t blocked_offset(int64_t i, int64_t j, int64_t cols)
+{
+    return (((i / DN_BM) * (cols / DN_BK) + j / DN_BK) * DN_BM + i % DN_BM) * DN_BK + j % DN_BK;
+}
+
+// Row-major (rows x cols) -> K-blocked order; one thread per 16-byte group of 8 elements.
+__global__ void block_k64(const __nv_bfloat16 *in, int64_t rows, int64_t cols, __nv_bfloat16 *out)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= rows * cols / 8) return;
+    const int64_t i = g / (cols / 8), j = (g % (cols / 8)) * 8;
+    *reinterpret_cast<int4 *>(out + blocked_offset(i, j, cols)) = *reinterpret_cast<const int4 *>(in + i * cols + j);
 }
 
 // 32x32 tiled transpose of a BF16 matrix (rows x cols) into (cols x rows).
@@ -424,7 +505,7 @@ static EncodeTiledFn encode_fn()
     return fn;
 }
 
-// Row-major BF16 matrix (rows x cols) viewed with boxes of DN_BK columns (64 bytes) x box_rows rows.
+// Row-major BF16 matrix (rows x cols) viewed with boxes of DN_BK columns (128 bytes) x box_rows rows.
 static sme_status make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int box_rows)
 {
     EncodeTiledFn fn = encode_fn();
@@ -437,7 +518,7 @@ static sme_status make_map(CUtensorMap *map, const void *base, int64_t rows, int
     const cuuint32_t box[2] = {(cuuint32_t)DN_BK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -446,10 +527,17 @@ static sme_status make_map(CUtensorMap *map, const void *base, int64_t rows, int
     return SME_OK;
 }
 
+// K-blocked matrix (rows x cols) viewed as (rows * cols / 64) rows of 64 elements, boxes of 128 such rows:
+// box y = (t * cols/64 + kb) * 128 is the 128 x 64 block of row tile t and K-block kb.
+static sme_status make_map_blocked(CUtensorMap *map, const void *base, int64_t rows, int64_t cols)
+{
+    return make_map(map, base, rows * cols / DN_BK, DN_BK, DN_BM);
+}
+
 static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 template <int KP>
-static size_t dense_smem() { return (size_t)DenseCfg<KP>::STAGES * DenseCfg<KP>::STAGE + 1024; }
+static size_t dense_smem() { return (size_t)DenseCfg<KP>::BYTES + 1024; }
 
 static sme_status ensure_dense_workspace(sme_op op, int kp)
 {
@@ -461,8 +549,8 @@ static sme_status ensure_dense_workspace(sme_op op, int kp)
         D->Bf[b] = D->Bb[b] = nullptr;
         SME_TRY(dev_alloc(op, (void **)&D->Bf[b], (size_t)2 * kp * D->n * 2));
         SME_TRY(dev_alloc(op, (void **)&D->Bb[b], (size_t)2 * kp * D->m * 2));
-        SME_TRY(make_map(&D->mapBf[b], D->Bf[b], 2 * kp, D->n, 256));
-        SME_TRY(make_map(&D->mapBb[b], D->Bb[b], 2 * kp, D->m, 256));
+        SME_TRY(make_map(&D->mapBf[b], D->Bf[b], 2 * kp, D->n, 128));
+        SME_TRY(make_map(&D->mapBb[b], D->Bb[b], 2 * kp, D->m, 128));
     }
     // Each buffer on its own, so that a call after a failed allocation completes the set.
     if (!D->x[0]) SME_TRY(dev_alloc(op, (void **)&D->x[0], D->m * 4));
@@ -482,8 +570,19 @@ static sme_status launch_dense(const DenseMaps &maps, const DenseArgs &a, int gr
         SME_CUDA(cudaFuncSetAttribute(dense_iteration<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr_set = true;
     }
-    dense_iteration<KP><<<grid, DN_THREADS, smem, s>>>(maps, a);
-    SME_CUDA(cudaGetLastError());
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(DN_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SME_CUDA(cudaLaunchKernelEx(&cfg, dense_iteration<KP>, maps, a));
     return SME_OK;
 }
 
@@ -495,7 +594,7 @@ static sme_status run_dense(sme_op op, const DenseArgs &a, int buf, cudaStream_t
     maps.X[1] = D->mapAt;
     maps.B[0] = D->mapBf[buf];
     maps.B[1] = D->mapBb[buf];
-    const int grid = (int)(D->m / DN_BM + D->n / DN_BM);
+    const int grid = a.row_ctas + ((a.col_tiles + 1) & ~1);  // whole clusters of two on each product
     if (a.kp == 256) return launch_dense<256>(maps, a, grid, s);
     return launch_dense<128>(maps, a, grid, s);
 }
@@ -507,6 +606,8 @@ static DenseArgs dense_base(sme_op op, double alpha, double beta, double gamma, 
     a.m = D->m;
     a.n = D->n;
     a.row_tiles = (int)(D->m / DN_BM);
+    a.col_tiles = (int)(D->n / DN_BM);
+    a.row_ctas = (a.row_tiles + 1) & ~1;
     a.kp = kp;
     a.x[0] = D->x[0];
     a.x[1] = D->x[1];
@@ -609,18 +710,17 @@ __global__ void dense_sq(int64_t n, const float *x, const float *scale, double *
     sq[j] = e * c * c;
 }
 
-// out_i = own_i * sum_j X_ij^2 sq_j for X row-major (rows x cols, cols a multiple of 128), one warp per row,
-// 16-byte loads, FP64 accumulation; own_i = e^{2 x_i} (times c_i^2 for scaled rows).
+// out_i = own_i * sum_j X_ij^2 sq_j for X in K-blocked order (rows x cols, cols a multiple of 128), one warp
+// per row, 16-byte loads, FP64 accumulation; own_i = e^{2 x_i} (times c_i^2 for scaled rows).
 __global__ void dense_row_norms(const __nv_bfloat16 *X, int64_t rows, int64_t cols, const double *sq,
                                 const double *own, double *out)
 {
     const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (r >= rows) return;
-    const int4 *row = reinterpret_cast<const int4 *>(X + r * cols);
     double acc = 0.0;
     for (int64_t q = lane; q < cols / 8; q += 32) {
-        const int4 w = row[q];
+        const int4 w = *reinterpret_cast<const int4 *>(X + blocked_offset(r, q * 8, cols));
         const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&w);
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
@@ -685,6 +785,10 @@ extern "C" sme_status sme_op_create_dense(sme_op *out, int64_t m, int64_t n, con
         set_error("sme_op_create_dense: m and n must be positive multiples of 128, lda >= n");
         return SME_ERR_ARG;
     }
+    if (m * n / DN_BK > (int64_t)INT32_MAX) {
+        set_error("sme_op_create_dense: m * n must be below 2^37 (tile coordinates are 32-bit)");
+        return SME_ERR_UNSUPPORTED;
+    }
     if (dtype != SME_BF16 && dtype != SME_FP8E4M3) {
         set_error("sme_op_create_dense: dtype must be SME_BF16 or SME_FP8E4M3");
         return SME_ERR_ARG;
@@ -748,6 +852,23 @@ extern "C" sme_status sme_op_create_dense(sme_op *out, int64_t m, int64_t n, con
     }
     bf16_check_finite<<<152 * 4, 256, 0, s>>>(D->A, m * n, op->d_status);
     transpose_bf16<<<dim3((unsigned)(n / 32), (unsigned)(m / 32)), dim3(32, 8), 0, s>>>(D->A, m, n, D->At);
+    {
+        // Both copies into K-blocked order (each TMA tile one contiguous run): A into a new buffer, then A^T
+        // into A's old buffer; the row-major A^T is released.
+        __nv_bfloat16 *blk = nullptr;
+        if ((st = dev_alloc(op, (void **)&blk, (size_t)m * n * 2)) != SME_OK) {
+            cudaStreamSynchronize(s);
+            if (staging) cudaFree(staging);
+            return fail(st);
+        }
+        block_k64<<<nblk(m * n / 8), 256, 0, s>>>(D->A, m, n, blk);
+        block_k64<<<nblk(m * n / 8), 256, 0, s>>>(D->At, n, m, D->A);
+        __nv_bfloat16 *row_major_t = D->At;
+        D->At = D->A;
+        D->A = blk;
+        cudaStreamSynchronize(s);
+        dev_free(op, row_major_t, (size_t)m * n * 2);
+    }
     int st_h = 0;
     cudaMemcpyAsync(&st_h, op->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
@@ -760,8 +881,8 @@ extern "C" sme_status sme_op_create_dense(sme_op *out, int64_t m, int64_t n, con
         set_error("sme_op_create_dense: non-finite matrix value");
         return fail(SME_ERR_NONFINITE);
     }
-    if ((st = make_map(&D->mapA, D->A, m, n, DN_BM)) != SME_OK) return fail(st);
-    if ((st = make_map(&D->mapAt, D->At, n, m, DN_BM)) != SME_OK) return fail(st);
+    if ((st = make_map_blocked(&D->mapA, D->A, m, n)) != SME_OK) return fail(st);
+    if ((st = make_map_blocked(&D->mapAt, D->At, n, m)) != SME_OK) return fail(st);
     *out = op;
     return SME_OK;
 }
