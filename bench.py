@@ -940,6 +940,7 @@ def main():
         rp_h = torch.from_numpy(A.row_ptr).pin_memory()
         ci_h = torch.from_numpy(A.col_idx).pin_memory()
         va_h = torch.from_numpy(A.vals).pin_memory()
+        b_h = b.cpu().pin_memory()
         out_h = torch.empty(m + 2 * n, dtype=torch.float32).pin_memory()
         e2e_steps = max(1, min(args.steps, 5))
         barrier()
@@ -951,7 +952,8 @@ def main():
             sme.sme_equilibrate(op2, u2, v2, ub2, vb2, T=T, k=k, seed=0)
             x2 = torch.zeros(n, **f32)
             if do_lsqr:
-                sme.sme_lsqr(op2, ub2, vb2, b, x2, tol=1e-6, max_iters=20000, check_every=10)
+                b2 = b_h.to("cuda", non_blocking=True)  # this step's right-hand side, from pinned host memory
+                sme.sme_lsqr(op2, ub2, vb2, b2, x2, tol=1e-6, max_iters=20000, check_every=10)
             out_h[:m].copy_(ub2, non_blocking=True)
             out_h[m:m + n].copy_(vb2, non_blocking=True)
             out_h[m + n:].copy_(x2, non_blocking=True)
@@ -959,7 +961,7 @@ def main():
             sme.sme_op_destroy(op2)
         barrier()
         e2e_el = ranks.max(time.perf_counter() - t0)
-        h2d = 4 * (m + 1) + 8 * nnz + 4 * m  # CSR arrays + b
+        h2d = 4 * (m + 1) + 8 * nnz + (4 * m if do_lsqr else 0)  # CSR arrays + b
         e2e = {"value": world * units_per_step * e2e_steps / e2e_el, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 4 * (m + 2 * n), "steps": e2e_steps, "ms_per_step": 1e3 * e2e_el / e2e_steps}
 
