@@ -274,8 +274,9 @@ sme_status sme::create_csr_grouped(sme_op *out, int64_t m, int64_t n, int64_t nn
     }
     const size_t vsz = dtype == SME_F64 ? 8 : 4;
     cudaStream_t s = (cudaStream_t)stream;
-    // Host input is checked on a host thread while the device is set up; its verdict is taken before
-    // anything is built, and an invalid input is reported as such even when the device setup fails too.
+    // Host input is checked on a host thread while the device copies and builds it (the device build
+    // checks the same structure first and stops on a violation); an invalid input is reported with the
+    // host check's message, also when the device setup fails.
     HostValidation validation;
     if (!on_device)
         validation.start([=] {
@@ -316,14 +317,10 @@ sme_status sme::create_csr_grouped(sme_op *out, int64_t m, int64_t n, int64_t nn
         d_rp = (const int32_t *)tmp[0];
         d_col = (const int32_t *)tmp[1];
         d_val = tmp[2];
-        // The copies are in flight (overlapping the host check when the input is pinned).
-        if (validation.result() != SME_OK) {
-            cudaStreamSynchronize(s);
-            for (void *p : tmp)
-                if (p) cudaFree(p);
-            sme_op_destroy(op);
-            return validation.report();
-        }
+        // The copies are in flight, and the build below starts without waiting for the host check: the
+        // build's first step is the same check on the device, which gates every later kernel, so nothing
+        // reads out of bounds on invalid input.  The host check's verdict (its message names the row and
+        // the fault) is taken after the build.
     }
     uint32_t *groups[2] = {nullptr, nullptr};
     if (row_group_host && col_group_host) {
@@ -346,6 +343,10 @@ sme_status sme::create_csr_grouped(sme_op *out, int64_t m, int64_t n, int64_t nn
         if (p) cudaFree(p);
     for (void *p : groups)
         if (p) cudaFree(p);
+    if (validation.result() != SME_OK) {
+        sme_op_destroy(op);
+        return validation.report();
+    }
     if (st != SME_OK) {
         sme_op_destroy(op);
         return st;
