@@ -48,9 +48,11 @@ def _gpu_estimate(op, m, n, u, v, t, k, seed):
     return zu.cpu().double().numpy(), zv.cpu().double().numpy()
 
 
-@pytest.mark.parametrize("m,n", [(256, 256), (384, 256), (256, 512)])
+@pytest.mark.parametrize("m,n", [(256, 256), (384, 256), (256, 512), (1280, 384), (384, 2560)])
 @pytest.mark.parametrize("k", [128, 256])
 def test_dense_estimate_matches_oracle(m, n, k):
+    """Shapes with an odd number of 128-row tiles (384, 1280) exercise the spare CTA of the last cluster;
+    384 x 2560 runs more clusters than one per product."""
     Ad, Af = _bf16_matrix(m, n, seed=m + n + k)
     op = sme.sme_op_create_dense(m, n, Ad, dtype=sme.SME_BF16)
     try:
@@ -66,11 +68,12 @@ def test_dense_estimate_matches_oracle(m, n, k):
     assert np.all(np.abs(zv - ezv) <= _tol(m) * c2), np.max(np.abs(zv - ezv) / c2)
 
 
-def test_dense_every_step_matches_oracle():
-    """20 iterations of Algorithm 1 on a 256 x 384 dense matrix, k = 256, each step checked against the
-    oracle's step from the GPU's own state (norm-wise relative error of [u; v; ubar; vbar] <= 1e-4)."""
+@pytest.mark.parametrize("m,n", [(256, 384), (1280, 384)])
+def test_dense_every_step_matches_oracle(m, n):
+    """20 iterations of Algorithm 1 on a dense matrix, k = 256, each step checked against the oracle's step
+    from the GPU's own state (norm-wise relative error of [u; v; ubar; vbar] <= 1e-4)."""
     import torch
-    m, n, k = 256, 384, 256
+    k = 256
     Ad, Af = _bf16_matrix(m, n, seed=5)
     A64 = O.OracleCSR.from_any(Af.astype(np.float64))
     d = O.default_params(m, n)
