@@ -58,6 +58,19 @@ typedef enum {
 const char *sme_status_string(sme_status s);
 const char *sme_last_error(void);
 
+/*
+ * sme_release_cached_memory -- return the library's idle device memory to the system.
+ *
+ * The device buffers of destroyed operators (and the staging of host input during
+ * operator creation) are kept, by exact size, for later operators: creating and
+ * destroying an operator per solve then allocates nothing after the first time.
+ * Stream-ordered scratch of the device builds comes from a library memory pool that
+ * keeps its memory between calls.  This call frees every idle block and trims the
+ * pool; an allocation that fails does the same before trying again.  Operators that
+ * are alive are not affected.  Synchronises the device.  Always SME_OK.
+ */
+sme_status sme_release_cached_memory(void);
+
 /* ------------------------------------------------------------------ operators */
 
 /*

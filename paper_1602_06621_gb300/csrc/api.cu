@@ -8,8 +8,10 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 #include <thread>
 #include <vector>
 
@@ -51,6 +53,132 @@ static bool injected_alloc_failure()
     return calls++ == std::atoll(armed.c_str());
 }
 
+// ------------------------------------------------------------------ device memory
+// Operators are often created and destroyed once per solve, and cudaMalloc / cudaFree of a large
+// operator's buffers cost milliseconds.  Blocks of destroyed operators (and the host-input staging of
+// operator creation) are therefore kept, by exact size, for the next operator; stream-ordered scratch
+// comes from a library memory pool that keeps its memory between calls.  Only blocks whose last use has
+// completed enter the cache.  sme_release_cached_memory() returns both to the system, and an allocation
+// that fails first releases them and tries again.
+namespace {
+struct BlockCache {
+    std::mutex mu;
+    std::unordered_map<void *, size_t> live;    // blocks handed out by cache_alloc, with their sizes
+    std::multimap<size_t, void *> idle;          // retired blocks by size
+    size_t idle_bytes = 0;
+};
+BlockCache &block_cache()
+{
+    static BlockCache *c = new BlockCache();  // never destroyed: blocks may be retired during process exit
+    return *c;
+}
+constexpr size_t CACHE_CAP = size_t(32) << 30;  // idle bytes kept at most
+thread_local bool g_retiring = false;           // set by sme_op_destroy after its device synchronisation
+}  // namespace
+
+cudaMemPool_t scratch_pool()
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = pool;
+    }
+    return pools[dev];
+}
+
+static void release_cached_blocks()
+{
+    BlockCache &c = block_cache();
+    std::vector<void *> blocks;
+    {
+        std::lock_guard<std::mutex> lock(c.mu);
+        for (auto &kv : c.idle) blocks.push_back(kv.second);
+        c.idle.clear();
+        c.idle_bytes = 0;
+    }
+    for (void *p : blocks) cudaFree(p);
+    if (cudaMemPool_t pool = scratch_pool()) {
+        cudaDeviceSynchronize();
+        cudaMemPoolTrimTo(pool, 0);
+    }
+}
+
+cudaError_t cache_alloc(void **p, size_t bytes)
+{
+    BlockCache &c = block_cache();
+    {
+        std::lock_guard<std::mutex> lock(c.mu);
+        auto it = c.idle.find(bytes);
+        if (it != c.idle.end()) {
+            *p = it->second;
+            c.idle.erase(it);
+            c.idle_bytes -= bytes;
+            c.live[*p] = bytes;
+            return cudaSuccess;
+        }
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        release_cached_blocks();
+        e = cudaMalloc(p, bytes);
+    }
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e;
+    }
+    std::lock_guard<std::mutex> lock(c.mu);
+    c.live[*p] = bytes;
+    return cudaSuccess;
+}
+
+void cache_retire(void *p)
+{
+    if (!p) return;
+    BlockCache &c = block_cache();
+    {
+        std::lock_guard<std::mutex> lock(c.mu);
+        auto it = c.live.find(p);
+        if (it != c.live.end()) {
+            const size_t bytes = it->second;
+            c.live.erase(it);
+            if (c.idle_bytes + bytes <= CACHE_CAP) {
+                c.idle.emplace(bytes, p);
+                c.idle_bytes += bytes;
+                return;
+            }
+        }
+    }
+    cudaFree(p);
+}
+
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s)
+{
+    cudaMemPool_t pool = scratch_pool();
+    if (!pool) return cudaMallocAsync(p, bytes, s);
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        release_cached_blocks();
+        e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+    }
+    return e;
+}
+
 sme_status dev_alloc(sme_op op, void **p, size_t bytes)
 {
     *p = nullptr;
@@ -59,7 +187,7 @@ sme_status dev_alloc(sme_op op, void **p, size_t bytes)
         set_error("device allocation of %zu bytes failed: injected (SME_FAIL_DEV_ALLOC)", bytes);
         return SME_ERR_OOM;
     }
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = cache_alloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
@@ -70,10 +198,27 @@ sme_status dev_alloc(sme_op op, void **p, size_t bytes)
     return SME_OK;
 }
 
+// Releases an operator block: kept for reuse while its operator is being destroyed (the device is idle
+// then), freed at once otherwise.
+void dev_release(void *p)
+{
+    if (!p) return;
+    if (g_retiring) {
+        cache_retire(p);
+        return;
+    }
+    {
+        BlockCache &c = block_cache();
+        std::lock_guard<std::mutex> lock(c.mu);
+        c.live.erase(p);
+    }
+    cudaFree(p);
+}
+
 void dev_free(sme_op op, void *p, size_t bytes)
 {
     if (!p) return;
-    cudaFree(p);
+    dev_release(p);
     op->device_bytes -= (int64_t)(bytes == 0 ? 16 : bytes);
 }
 
@@ -81,7 +226,7 @@ static void free_sell(sme_op op, Sell &S)
 {
     for (void *p : {(void *)S.slice_off, (void *)S.slice_w, (void *)S.perm, (void *)S.iperm, (void *)S.len, S.ent,
                     (void *)S.val64})
-        if (p) cudaFree(p);
+        dev_release(p);
     S = Sell{};
     (void)op;
 }
@@ -219,16 +364,23 @@ extern "C" const char *sme_status_string(sme_status s)
 
 extern "C" const char *sme_last_error(void) { return g_err; }
 
+extern "C" sme_status sme_release_cached_memory(void)
+{
+    release_cached_blocks();
+    return SME_OK;
+}
+
 extern "C" sme_status sme_op_destroy(sme_op op)
 {
     if (!op) return SME_OK;
     cudaDeviceSynchronize();
+    g_retiring = true;  // nothing on the device uses this operator's memory any more
     free_sell(op, op->fwd);
     free_sell(op, op->bwd);
     Workspace &W = op->ws;
     for (void *p : {W.u, W.v, W.ub, W.vb, W.tab_u[0], W.tab_u[1], W.tab_v[0], W.tab_v[1], (void *)W.red, W.tgt[0],
                     W.tgt[1], (void *)W.sym_pos})
-        if (p) cudaFree(p);
+        dev_release(p);
     release_lsqr(op);
     if (op->graph.exec) cudaGraphExecDestroy(op->graph.exec);
     if (op->graph.stream) cudaStreamDestroy(op->graph.stream);
@@ -236,12 +388,13 @@ extern "C" sme_status sme_op_destroy(sme_op op)
     if (op->batch) {
         for (int side = 0; side < 2; ++side)
             for (void *p : {(void *)op->batch->mid[side], (void *)op->batch->loc[side], op->batch->tgt2[side]})
-                if (p) cudaFree(p);
+                dev_release(p);
         delete[] op->batch->row_off;
         delete[] op->batch->col_off;
         delete op->batch;
     }
-    if (op->d_status) cudaFree(op->d_status);
+    dev_release(op->d_status);
+    g_retiring = false;
     for (cudaEvent_t e : op->ev_loop)
         if (e) cudaEventDestroy(e);
     delete op;
@@ -302,10 +455,10 @@ sme_status sme::create_csr_grouped(sme_op *out, int64_t m, int64_t n, int64_t nn
                                  (size_t)std::max<int64_t>(nnz, 1) * vsz};
         const void *src[3] = {row_ptr, col_idx, vals};
         for (int i = 0; i < 3; ++i) {
-            if (cudaMalloc(&tmp[i], bytes[i]) != cudaSuccess) {
+            if (cache_alloc(&tmp[i], bytes[i]) != cudaSuccess) {
                 cudaGetLastError();
-                for (void *p : tmp)
-                    if (p) cudaFree(p);
+                cudaStreamSynchronize(s);
+                for (void *p : tmp) cache_retire(p);
                 sme_op_destroy(op);
                 if (validation.result() != SME_OK) return validation.report();
                 set_error("sme_op_create_csr: staging allocation failed");
@@ -339,8 +492,7 @@ sme_status sme::create_csr_grouped(sme_op *out, int64_t m, int64_t n, int64_t nn
     }
     st = build_sparse(op, d_rp, d_col, d_val, s, groups[0], groups[1], groups[0] && groups[1] ? group_bits : 0);
     cudaStreamSynchronize(s);
-    for (void *p : tmp)
-        if (p) cudaFree(p);
+    for (void *p : tmp) cache_retire(p);  // the copies and the build that read them have completed
     for (void *p : groups)
         if (p) cudaFree(p);
     if (validation.result() != SME_OK) {

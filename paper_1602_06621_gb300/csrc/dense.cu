@@ -544,8 +544,8 @@ static sme_status ensure_dense_workspace(sme_op op, int kp)
     DenseOp *D = op->dense;
     if (D->kcap >= kp) return SME_OK;
     for (int b = 0; b < 2; ++b) {
-        if (D->Bf[b]) cudaFree(D->Bf[b]);
-        if (D->Bb[b]) cudaFree(D->Bb[b]);
+        dev_free(op, D->Bf[b], D->Bf[b] ? (size_t)2 * D->kcap * D->n * 2 : 0);
+        dev_free(op, D->Bb[b], D->Bb[b] ? (size_t)2 * D->kcap * D->m * 2 : 0);
         D->Bf[b] = D->Bb[b] = nullptr;
         SME_TRY(dev_alloc(op, (void **)&D->Bf[b], (size_t)2 * kp * D->n * 2));
         SME_TRY(dev_alloc(op, (void **)&D->Bb[b], (size_t)2 * kp * D->m * 2));
@@ -631,7 +631,7 @@ void dense_destroy(sme_op op)
     for (void *p : {(void *)D->A, (void *)D->At, (void *)D->row_scale, (void *)D->Bf[0], (void *)D->Bf[1],
                     (void *)D->Bb[0], (void *)D->Bb[1], (void *)D->x[0], (void *)D->x[1], (void *)D->xb[0],
                     (void *)D->xb[1]})
-        if (p) cudaFree(p);
+        dev_release(p);
     delete D;
     op->dense = nullptr;
 }

@@ -561,7 +561,7 @@ void release_lsqr(sme_op op)
     if (!L) return;
     for (void *p : {L->ud, L->ve, L->w, L->x, L->d, L->e, L->bs, L->xt, (void *)L->r, (void *)L->partials,
                     (void *)L->counter, (void *)L->sc})
-        if (p) cudaFree(p);
+        dev_release(p);
     delete L->host;
     delete L;
     op->ws.lsqr = nullptr;

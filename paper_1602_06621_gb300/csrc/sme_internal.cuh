@@ -30,6 +30,12 @@ sme_status cuda_fail(cudaError_t e, const char *what, int line);
         if (_s != SME_OK) return _s;         \
     } while (0)
 
+// Device memory (api.cu).  cache_alloc / cache_retire: blocks reused by exact size once retired (only
+// after their last use has completed); scratch_alloc: stream-ordered memory from the library's pool.
+cudaError_t cache_alloc(void **p, size_t bytes);
+void cache_retire(void *p);
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s);
+
 // Stream-ordered scratch that is released when its scope ends, on every return path (including the early
 // returns of SME_CUDA / SME_TRY).
 struct AsyncScratch {
@@ -42,7 +48,7 @@ struct AsyncScratch {
     }
     AsyncScratch(const AsyncScratch &) = delete;
     AsyncScratch &operator=(const AsyncScratch &) = delete;
-    cudaError_t alloc(size_t bytes) { return cudaMallocAsync(&p, bytes, s); }
+    cudaError_t alloc(size_t bytes) { return scratch_alloc(&p, bytes, s); }
     template <typename T>
     T *as() const { return static_cast<T *>(p); }
 };
@@ -213,6 +219,9 @@ namespace sme {
 // Device allocation bookkeeping for an op.
 sme_status dev_alloc(sme_op op, void **p, size_t bytes);
 void dev_free(sme_op op, void *p, size_t bytes);
+// Releases a dev_alloc block without accounting (the operator is being destroyed, or the caller keeps
+// the count): kept for reuse inside sme_op_destroy, freed at once elsewhere.
+void dev_release(void *p);
 
 // Build-time device utilities (build_kernels.cu).
 sme_status scan_exclusive_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);  // out[n] = total

@@ -23,7 +23,7 @@ __all__ = [
     "sme_equilibrate_targets", "sme_equilibrate_symmetric", "sme_equilibrate_block", "sme_mlp_create",
     "sme_mlp_destroy", "sme_mlp_param_count", "sme_mlp_get_params", "sme_mlp_set_params", "sme_mlp_forward",
     "sme_mlp_gradient", "sme_mlp_train_step", "sme_op_features", "sme_warm_start", "sme_batch_evaluate",
-    "sme_batch_features", "sme_batch_warm_start", "sme_op_norm2", "sme_ccp_lasso",
+    "sme_batch_features", "sme_batch_warm_start", "sme_op_norm2", "sme_ccp_lasso", "sme_release_cached_memory",
 ]
 SME_STATIC_MAX_COLS = 1 << 20
 
@@ -89,6 +89,7 @@ _vp, _i64, _i32, _u64, _d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, cty
 SIGNATURES = {
     "sme_status_string": ([_i32], ctypes.c_char_p),
     "sme_last_error": ([], ctypes.c_char_p),
+    "sme_release_cached_memory": ([], _i32),
     "sme_op_create_csr": ([ctypes.POINTER(_vp), _i64, _i64, _i64, _vp, _vp, _vp, _i32, _i32, _vp], _i32),
     "sme_op_create_dense": ([ctypes.POINTER(_vp), _i64, _i64, _vp, _i64, _i32, _vp, _i32, _vp], _i32),
     "sme_op_destroy": ([_vp], _i32),
@@ -172,6 +173,10 @@ def _ptr(x):
 
 def sme_status_string(status: int) -> str:
     return load().sme_status_string(status).decode()
+
+
+def sme_release_cached_memory() -> None:
+    _check(load().sme_release_cached_memory(), "sme_release_cached_memory")
 
 
 def default_params(m: int, n: int) -> dict:
