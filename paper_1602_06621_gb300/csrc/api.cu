@@ -62,11 +62,21 @@ static bool injected_alloc_failure()
 // that fails first releases them and tries again.
 namespace {
 struct BlockCache {
+    using Key = std::pair<int, size_t>;          // (device, bytes)
     std::mutex mu;
-    std::unordered_map<void *, size_t> live;    // blocks handed out by cache_alloc, with their sizes
-    std::multimap<size_t, void *> idle;          // retired blocks by size
+    std::unordered_map<void *, Key> live;        // blocks handed out by cache_alloc
+    std::multimap<Key, void *> idle;             // retired blocks
     size_t idle_bytes = 0;
 };
+int current_device()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return dev;
+}
 BlockCache &block_cache()
 {
     static BlockCache *c = new BlockCache();  // never destroyed: blocks may be retired during process exit
@@ -120,14 +130,15 @@ static void release_cached_blocks()
 cudaError_t cache_alloc(void **p, size_t bytes)
 {
     BlockCache &c = block_cache();
+    const BlockCache::Key key(current_device(), bytes);
     {
         std::lock_guard<std::mutex> lock(c.mu);
-        auto it = c.idle.find(bytes);
+        auto it = c.idle.find(key);
         if (it != c.idle.end()) {
             *p = it->second;
             c.idle.erase(it);
             c.idle_bytes -= bytes;
-            c.live[*p] = bytes;
+            c.live[*p] = key;
             return cudaSuccess;
         }
     }
@@ -142,7 +153,7 @@ cudaError_t cache_alloc(void **p, size_t bytes)
         return e;
     }
     std::lock_guard<std::mutex> lock(c.mu);
-    c.live[*p] = bytes;
+    c.live[*p] = key;
     return cudaSuccess;
 }
 
@@ -154,11 +165,11 @@ void cache_retire(void *p)
         std::lock_guard<std::mutex> lock(c.mu);
         auto it = c.live.find(p);
         if (it != c.live.end()) {
-            const size_t bytes = it->second;
+            const BlockCache::Key key = it->second;
             c.live.erase(it);
-            if (c.idle_bytes + bytes <= CACHE_CAP) {
-                c.idle.emplace(bytes, p);
-                c.idle_bytes += bytes;
+            if (c.idle_bytes + key.second <= CACHE_CAP) {
+                c.idle.emplace(key, p);
+                c.idle_bytes += key.second;
                 return;
             }
         }
