@@ -351,8 +351,8 @@ __global__ void lsqr_init_rows(int64_t m, const int32_t *perm, const real *b, co
     __threadfence();
     double v1 = 0.0, v2 = 0.0;
     for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
-        v1 += ((volatile double *)partials)[i];
-        v2 += ((volatile double *)partials)[gridDim.x + i];
+        v1 += __ldcg(partials + i);
+        v2 += __ldcg(partials + gridDim.x + i);
     }
     const double t1 = block_sum(v1);
     const double t2 = block_sum(v2);

@@ -53,8 +53,11 @@ __device__ __forceinline__ bool arrive_last(double part, double *partials, unsig
 __device__ __forceinline__ double sum_partials(const double *partials, unsigned *counter)
 {
     __threadfence();
+    // Loads through L2 (the partials come from other SMs), several in flight per thread; each thread still
+    // adds its partials in index order.
     double v = 0.0;
-    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) v += ((volatile const double *)partials)[i];
+#pragma unroll 4
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) v += __ldcg(partials + i);
     const double s = block_sum(v);
     __shared__ double res;
     if (threadIdx.x == 0) {
