@@ -879,7 +879,7 @@ def main():
             ev_mid[1].record(stream)
         res = None
         if do_lsqr:
-            res = sme.sme_lsqr(op, ub, vb, b, x, tol=1e-6, max_iters=20000, check_every=10)
+            res = sme.sme_lsqr(op, ub, vb, b, x, tol=1e-6, max_iters=20000, check_every=10, predict_check=True)
         if record:
             ev_mid[2].record(stream)
             ev_mid[2].synchronize()
@@ -953,7 +953,7 @@ def main():
             x2 = torch.zeros(n, **f32)
             if do_lsqr:
                 b2 = b_h.to("cuda", non_blocking=True)  # this step's right-hand side, from pinned host memory
-                sme.sme_lsqr(op2, ub2, vb2, b2, x2, tol=1e-6, max_iters=20000, check_every=10)
+                sme.sme_lsqr(op2, ub2, vb2, b2, x2, tol=1e-6, max_iters=20000, check_every=10, predict_check=True)
             out_h[:m].copy_(ub2, non_blocking=True)
             out_h[m:m + n].copy_(vb2, non_blocking=True)
             out_h[m + n:].copy_(x2, non_blocking=True)

@@ -248,6 +248,10 @@ typedef struct {
     int32_t stop_rule;   /* 0: ||A x - b|| / ||b||;  1: ||A^T r|| / (||A||_F ||r||) (least squares) */
     double *history;     /* HOST, may be NULL: the selected residual at every check, in order (sme_lsqr only) */
     int64_t history_cap; /* entries history can hold */
+    int32_t predict_check; /* sme_lsqr, stop_rule 0, tol > 0: bring a check forward to the iteration at which
+                              the geometric trend of the last two checked residuals (the first being 1 at
+                              x = 0) reaches tol; checks stay at most check_every apart, and stopping still
+                              rests only on the checked FP64 residual */
 } sme_lsqr_params;
 
 typedef struct {

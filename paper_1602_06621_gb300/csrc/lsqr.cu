@@ -658,8 +658,17 @@ static sme_status lsqr_t(sme_op op, const real *ubar, const real *vbar, const re
     GraphOnce chunk_graph;
     if (p->max_iters >= 2 * (int64_t)every) chunk_graph.capture([&](cudaStream_t q) { enqueue_chunk(every, q); });
     int64_t it = 0, hcount = 0;
+    // Predicted checks: the last two checked residuals (the first is 1 at x = 0) give a geometric trend.
+    const bool predict = p->predict_check && p->stop_rule == 0 && p->tol > 0.0;
+    double res_prev = 1.0, res_last = 1.0;
+    int64_t it_prev = 0, it_last = 0;
     while (it < p->max_iters) {
-        const int64_t chunk = std::min<int64_t>(every, p->max_iters - it);
+        int64_t chunk = std::min<int64_t>(every, p->max_iters - it);
+        if (predict && it_last > it_prev && res_last > p->tol && res_last < res_prev) {
+            const double per_iter = std::log(res_last / res_prev) / (double)(it_last - it_prev);  // < 0
+            const double need = std::ceil(std::log(p->tol / res_last) / per_iter);
+            if (need < (double)chunk) chunk = std::max<int64_t>(1, (int64_t)need);
+        }
         if (chunk == every && chunk_graph.exec)
             SME_CUDA(cudaGraphLaunch(chunk_graph.exec, s));
         else
@@ -673,6 +682,12 @@ static sme_status lsqr_t(sme_op op, const real *ubar, const real *vbar, const re
             p->history[hcount] = p->stop_rule == 1 ? L->host->normal_res : L->host->rel_res;
         ++hcount;
         if (L->host->done) break;
+        if (std::isfinite(L->host->rel_res)) {
+            res_prev = res_last;
+            it_prev = it_last;
+            res_last = L->host->rel_res;
+            it_last = it;
+        }
     }
     // Final x in original order, and both residuals of exactly that x.
     lsqr_current_x<real><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, e, x, w, L->sc, xt, B.perm, x_out);

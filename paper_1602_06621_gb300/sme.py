@@ -74,7 +74,8 @@ class sme_ccp_result(ctypes.Structure):
 
 class sme_lsqr_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int64), ("check_every", ctypes.c_int32),
-                ("stop_rule", ctypes.c_int32), ("history", ctypes.c_void_p), ("history_cap", ctypes.c_int64)]
+                ("stop_rule", ctypes.c_int32), ("history", ctypes.c_void_p), ("history_cap", ctypes.c_int64),
+                ("predict_check", ctypes.c_int32)]
 
 
 class sme_lsqr_result(ctypes.Structure):
@@ -257,13 +258,14 @@ def sme_evaluate(op, u, v, alpha=0.0, beta=0.0, gamma=0.0, r2=None, c2=None, str
 
 
 def sme_lsqr(op, u_bar, v_bar, b, x, *, tol=1e-6, max_iters=100000, check_every=10, stop_rule=0, stream=None,
-             raise_on_not_converged=False, history=False) -> dict:
+             raise_on_not_converged=False, history=False, predict_check=False) -> dict:
     """LSQR on D A E (Section 5.1).  With history=True the result's "history" lists the checked residual
-    at every check (every check_every iterations)."""
-    cap = (int(max_iters) // max(1, int(check_every)) + 1) if history else 0
+    at every check (every check_every iterations, or earlier ones with predict_check)."""
+    cap = (int(max_iters) + 1) if history and predict_check else \
+        ((int(max_iters) // max(1, int(check_every)) + 1) if history else 0)
     hist = np.zeros(max(cap, 1))
     p = sme_lsqr_params(float(tol), int(max_iters), int(check_every), int(stop_rule),
-                        ctypes.c_void_p(hist.ctypes.data) if cap else None, cap)
+                        ctypes.c_void_p(hist.ctypes.data) if cap else None, cap, 1 if predict_check else 0)
     res = sme_lsqr_result()
     st = load().sme_lsqr(op, _ptr(u_bar), _ptr(v_bar), _ptr(b), _ptr(x), ctypes.byref(p), ctypes.byref(res),
                          _stream(stream))

@@ -77,6 +77,26 @@ def test_consistent_system_converges_and_reports_its_residual(small):
     assert ro.converged and abs(res["iters"] - ro.iters) <= max(3, 0.1 * ro.iters)
 
 
+def test_predicted_checks_stop_between_exact_and_fixed_cadence(small):
+    """With predict_check the solve stops at a checked FP64 residual <= tol: not before the first iteration
+    that reaches it (a check after every iteration finds that one), and at most check_every iterations
+    after it; the residual it reports is that of the x it returns.  With tol = 0 nothing is predicted."""
+    A, op, dt = small
+    b = O.csr_matvec(A, I.normal_vector(A.n, 6))
+    _, _, ub, vb = gpu_equilibrate(op, dt, A.m, A.n, T=200, k=1, seed=0)
+    _, exact = _gpu_lsqr(op, dt, ub, vb, b, A.n, tol=1e-6, max_iters=20000, check_every=1)
+    _, fixed = _gpu_lsqr(op, dt, ub, vb, b, A.n, tol=1e-6, max_iters=20000, check_every=25)
+    x, pred = _gpu_lsqr(op, dt, ub, vb, b, A.n, tol=1e-6, max_iters=20000, check_every=25, predict_check=True,
+                        history=True)
+    assert pred["converged"] == 1 and pred["rel_residual"] <= 1e-6
+    assert pred["rel_residual"] == pytest.approx(_rel_res(A, x, b), rel=1e-9)
+    assert exact["iters"] <= pred["iters"] <= exact["iters"] + 25, (exact["iters"], pred["iters"], fixed["iters"])
+    assert len(pred["history"]) == pred["history_count"] >= 2 and pred["history"][-1] <= 1e-6
+    _, zero = _gpu_lsqr(op, dt, ub, vb, b, A.n, tol=0.0, max_iters=50, check_every=10, predict_check=True,
+                        history=True)
+    assert zero["history_count"] == 5
+
+
 def test_equilibration_cuts_gpu_lsqr_iterations(small):
     """Section 5.1 on the GPU: the equilibrated system needs far fewer LSQR iterations."""
     A, op, dt = small
