@@ -373,7 +373,7 @@ __global__ void lsqr_init_rows(int64_t m, const int32_t *perm, const real *b, co
 
 // Products with A (rows): uhat = K v_i - alpha_i u_i; beta_{i+1} = ||uhat||.
 template <typename real, int SPLIT>
-__global__ void __launch_bounds__(LQ_THREADS) lsqr_rows(Sell S, const real *d, const real *ve, real *ud,
+__global__ void __launch_bounds__(LQ_THREADS, 8) lsqr_rows(Sell S, const real *d, const real *ve, real *ud,
                                                          double *partials, unsigned *counter, LsqrScalars *sc)
 {
     if (((volatile LsqrScalars *)sc)->done) return;  // the same for every thread of the block
