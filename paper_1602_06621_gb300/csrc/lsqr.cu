@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(LQ_THREADS, 8) lsqr_rows(Sell S, const real *d
 // vhat = K^T u_{i+1} - beta_{i+1} v_i, alpha_{i+1} = ||vhat||, and the scalar recurrence of iteration i.
 // init = 1 computes vhat = K^T u_1 only (alpha_1, rhobar_1).
 template <typename real, int SPLIT>
-__global__ void __launch_bounds__(LQ_THREADS) lsqr_cols(Sell S, const real *e, const real *ud, real *ve, real *w,
+__global__ void __launch_bounds__(LQ_THREADS, 8) lsqr_cols(Sell S, const real *e, const real *ud, real *ve, real *w,
                                                          real *x, double *partials, unsigned *counter,
                                                          LsqrScalars *sc, int init)
 {
