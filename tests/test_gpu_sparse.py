@@ -339,3 +339,30 @@ def test_long_rows_fp32_estimate(k):
     tol = 2 * L * 2.0 ** -24
     assert np.all(np.abs(zu - O.row_estimate(A, u32, v32, O.probe_signs(1, 2, 0, A.n, k))) <= tol * r2)
     assert np.all(np.abs(zv - O.col_estimate(A, u32, v32, O.probe_signs(1, 2, 1, A.m, k))) <= tol * c2)
+
+
+@pytest.mark.parametrize("mutate,code,text", [
+    (lambda rp, col, val: rp.__setitem__(1, 4), "SME_ERR_INVALID_CSR", "row"),
+    (lambda rp, col, val: col.__setitem__(4, 9), "SME_ERR_INVALID_CSR", "row"),
+    (lambda rp, col, val: col.__setitem__(1, 0), "SME_ERR_INVALID_CSR", "row"),
+    (lambda rp, col, val: rp.__setitem__(3, 4), "SME_ERR_INVALID_CSR", "nnz"),
+    (lambda rp, col, val: val.__setitem__(2, np.nan), "SME_ERR_NONFINITE", "row"),
+])
+def test_invalid_host_csr_on_the_device_path(mutate, code, text):
+    """Host input is checked on a host thread while the device copies and builds it (the build checks the
+    same structure first); an invalid input comes back with the host check's code and message, and the
+    library stays usable."""
+    rp = np.array([0, 2, 3, 5], np.int32)
+    col = np.array([0, 2, 1, 0, 3], np.int32)
+    val = np.array([1.0, -2.0, 3.0, 0.5, 4.0])
+    mutate(rp, col, val)
+    with pytest.raises(sme.SmeError) as ei:
+        sme.sme_op_create_csr(3, 4, rp, col, val)
+    assert ei.value.name == code and text in str(ei.value)
+    A = I.sparse_uniform_density(50, 40, 0.1, seed=3)
+    op = sme.sme_op_create_csr(A.m, A.n, A.row_ptr, A.col_idx, A.vals)
+    try:
+        got = gpu_equilibrate(op, sme.SME_F64, A.m, A.n, T=3, k=2, seed=1)
+    finally:
+        sme.sme_op_destroy(op)
+    assert rel_norm(got, O.equilibrate(A, T=3, k=2, seed=1)) <= 1e-10
