@@ -316,6 +316,10 @@ struct LsqrState {
     int64_t bytes;
     int64_t fwd_blocks, bwd_blocks;
     double afro;  // cached ||A||_F (< 0: not computed)
+    // The graph of one chunk of check_every iterations and its check, kept for later calls on this op (it
+    // reads only the op's own buffers); rebuilt when check_every or the stop rule changes.
+    cudaGraphExec_t chunk = nullptr;
+    int chunk_every = 0, chunk_rule = -1;
 };
 
 
@@ -562,6 +566,7 @@ void release_lsqr(sme_op op)
     for (void *p : {L->ud, L->ve, L->w, L->x, L->d, L->e, L->bs, L->xt, (void *)L->r, (void *)L->partials,
                     (void *)L->counter, (void *)L->sc})
         dev_release(p);
+    if (L->chunk) cudaGraphExecDestroy(L->chunk);
     delete L->host;
     delete L;
     op->ws.lsqr = nullptr;
@@ -655,8 +660,18 @@ static sme_status lsqr_t(sme_op op, const real *ubar, const real *vbar, const re
         SPLIT_LAUNCH(lsqr_residual, real, pf, q, F, xt, bs, L->r, L->partials, L->counter, L->sc, 0);
         if (p->stop_rule == 1) SPLIT_LAUNCH(lsqr_normal, real, pb, q, B, L->r, L->partials, L->counter, L->sc, 0);
     };
-    GraphOnce chunk_graph;
-    if (p->max_iters >= 2 * (int64_t)every) chunk_graph.capture([&](cudaStream_t q) { enqueue_chunk(every, q); });
+    if (L->chunk && (L->chunk_every != every || L->chunk_rule != p->stop_rule)) {
+        cudaGraphExecDestroy(L->chunk);
+        L->chunk = nullptr;
+    }
+    if (!L->chunk && p->max_iters >= 2 * (int64_t)every) {
+        GraphOnce g;
+        g.capture([&](cudaStream_t q) { enqueue_chunk(every, q); });
+        L->chunk = g.exec;
+        g.exec = nullptr;
+        L->chunk_every = every;
+        L->chunk_rule = p->stop_rule;
+    }
     int64_t it = 0, hcount = 0;
     // Predicted checks: the last two checked residuals (the first is 1 at x = 0) give a geometric trend.
     const bool predict = p->predict_check && p->stop_rule == 0 && p->tol > 0.0;
@@ -669,8 +684,8 @@ static sme_status lsqr_t(sme_op op, const real *ubar, const real *vbar, const re
             const double need = std::ceil(std::log(p->tol / res_last) / per_iter);
             if (need < (double)chunk) chunk = std::max<int64_t>(1, (int64_t)need);
         }
-        if (chunk == every && chunk_graph.exec)
-            SME_CUDA(cudaGraphLaunch(chunk_graph.exec, s));
+        if (chunk == every && L->chunk)
+            SME_CUDA(cudaGraphLaunch(L->chunk, s));
         else
             enqueue_chunk(chunk, s);
         it += chunk;
