@@ -99,12 +99,19 @@ sme_status sme_op_create_csr(sme_op *out, int64_t m, int64_t n, int64_t nnz, con
  * dtype SME_FP8E4M3: A is e4m3 (one byte per entry), row_scales[m] floats with
  *   A_ij = row_scales[i] * e4m3(A_ij); pass NULL for unit scales.
  * Products with the +-1 probe blocks run on the tcgen05 tensor cores with FP32
- * accumulation (Section 3.1 estimator, dense A).  m and n must be multiples of 128.
- * on_device as for the CSR form.  Synchronises `stream`.
+ * accumulation (Section 3.1 estimator, dense A).  m and n must be multiples of 128,
+ * and m*n below 2^37 (SME_ERR_UNSUPPORTED otherwise).  The op holds A and A^T (2 bytes
+ * per entry each) in a K-blocked order.  on_device as for the CSR form.  Synchronises
+ * `stream`.
  */
 sme_status sme_op_create_dense(sme_op *out, int64_t m, int64_t n, const void *A, int64_t lda, sme_dtype dtype,
                                const float *row_scales, int on_device, void *stream);
 
+/*
+ * sme_op_destroy -- release an operator (NULL is allowed).  Synchronises the device; the
+ * op's device blocks are then kept for reuse by later operators of the same sizes (see
+ * sme_release_cached_memory).  Always SME_OK.
+ */
 sme_status sme_op_destroy(sme_op op);
 
 typedef struct {
