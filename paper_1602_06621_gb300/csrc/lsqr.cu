@@ -282,7 +282,7 @@ static sme_status batch_evaluate_t(sme_op op, const real *u, const real *v, doub
 // ------------------------------------------------------------------ LSQR
 //
 // Paige & Saunders (1982) LSQR on K = D A E, used as in Section 5.1: solve K xbar = D b from
-// xbar = 0 and return x = E xbar; accuracy is judged on the original system.
+// xbar = 0 and return x = E xbar; accuracy is measured on the original system.
 //
 // Vectors live in sorted order.  The products gather pre-scaled vectors so each nonzero costs a
 // single gather: ud = D uhat (uhat = beta u, unnormalised) for the products with A^T, and

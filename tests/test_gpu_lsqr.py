@@ -3,7 +3,7 @@
 LSQR is a Lanczos process: two correct implementations that round differently
 drift apart as orthogonality is lost, so iterates are compared over the first
 few iterations (where rounding has not been amplified), and longer solves are
-judged by what LSQR promises: the residual of the returned x.  The residual the
+assessed by what LSQR promises: the residual of the returned x.  The residual the
 library reports is re-computed here from its x by the oracle in FP64.
 """
 import numpy as np
