@@ -52,6 +52,19 @@ def kernel_source_hash():
     h.update(_section(KERNEL_SOURCE, b"struct SellArgs", b"// Load a start state"))
     h.update(_section(KERNEL_HEADER, b"Philox4x32-10", b"------ operator"))
     return h.hexdigest()
+
+
+DENSE_SOURCE = os.path.join(ROOT, "paper_1602_06621_gb300", "csrc", "dense.cu")
+DENSE_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dense_iteration_bf16_k256.txt")
+
+
+def dense_source_hash():
+    """Hash of the dense iteration kernel's device code in dense.cu (configuration, PTX helpers, the kernel),
+    and the Philox section of the internal header."""
+    h = hashlib.sha256()
+    h.update(_section(DENSE_SOURCE, b"constexpr int DN_BM", b"// Operand of iteration t from a state vector"))
+    h.update(_section(KERNEL_HEADER, b"Philox4x32-10", b"------ operator"))
+    return h.hexdigest()
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sgd_iteration_f32_k32_large.txt")
 # Random 8-byte gathers per second from L2-resident tables, measured on GB300 by
 # paper_1602_06621_gb300/microbench/gather_ceiling.cu (profiles/sgd_iteration_f32_k32_large.txt): the second
@@ -115,12 +128,13 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def recorded_traffic():
-    """ncu DRAM bytes per launch of the iteration kernel, if taken on the current kernel source."""
+def recorded_traffic(path=None, source_hash=None):
+    """ncu DRAM bytes per launch recorded in a profile summary (default: the sparse iteration kernel's), if
+    taken on the current kernel source."""
     try:
-        src = kernel_source_hash()
+        src = (source_hash or kernel_source_hash)()
         vals = {}
-        for line in open(TRAFFIC_FILE):
+        for line in open(path or TRAFFIC_FILE):
             if "=" in line and not line.lstrip().startswith("#"):
                 key, val = line.split("=", 1)
                 vals[key.strip()] = val.strip()
@@ -388,7 +402,7 @@ def run_dense(args, rank, world, local):
                                f"column factors; k={k} +-1 probes (two-term BF16 scalings), FP32 accumulation; T={T}",
                    "m": N, "n": N, "k": k, "T": T, "l2": "inputs larger than L2 (A: 512 MB)"},
         "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
-                     "traffic": None, "peak_kind": kind + " (bf16 sustained)",
+                     "traffic": recorded_traffic(DENSE_TRAFFIC_FILE, dense_source_hash), "peak_kind": kind + " (bf16 sustained)",
                      "kernel": "dense_iteration<256> (one iteration, both products)",
                      "algorithmic_flops_per_launch": flops, "executed_flops_per_launch": 2 * flops,
                      "launch_us": bf["iter_s"] * 1e6, "hbm_gbs": 2 * 2.0 * N * N / bf["iter_s"] / 1e9},
