@@ -173,10 +173,12 @@ def _ptr(x):
 
 
 def sme_status_string(status: int) -> str:
+    """Short name of a status code (`sme_status_string` in include/sme.h)."""
     return load().sme_status_string(status).decode()
 
 
 def sme_release_cached_memory() -> None:
+    """Return the library's idle device memory (blocks of destroyed operators, pool scratch) to the device."""
     _check(load().sme_release_cached_memory(), "sme_release_cached_memory")
 
 
@@ -209,6 +211,7 @@ def sme_op_create_csr(m, n, row_ptr, col_idx, vals, dtype=None, stream=None):
 
 
 def sme_op_create_dense(m, n, A, lda=None, dtype=SME_BF16, row_scales=None, stream=None):
+    """Create a dense operator (BF16, or FP8-E4M3 with per-row scales); m and n multiples of 128."""
     on_device = not isinstance(A, np.ndarray)
     op = ctypes.c_void_p()
     st = load().sme_op_create_dense(ctypes.byref(op), int(m), int(n), _ptr(A), int(lda if lda else n), int(dtype),
@@ -218,23 +221,27 @@ def sme_op_create_dense(m, n, A, lda=None, dtype=SME_BF16, row_scales=None, stre
 
 
 def sme_op_destroy(op):
+    """Destroy an operator; its device blocks are kept for reuse by later operators of the same sizes."""
     if op:
         _check(load().sme_op_destroy(op), "sme_op_destroy")
 
 
 def sme_op_get_info(op) -> dict:
+    """Sizes, dtype, device bytes and the last timed iteration loop of an operator, as a dict."""
     info = sme_op_info()
     _check(load().sme_op_get_info(op, ctypes.byref(info)), "sme_op_get_info")
     return {f: getattr(info, f) for f, _ in sme_op_info._fields_}
 
 
 def sme_draw_probes(seed, t, stream_id, length, k, words, stream=None):
+    """Write the bit-packed +-1 probes of iteration t (Philox4x32-10 contract) into `words`."""
     _check(load().sme_draw_probes(int(seed), int(t), int(stream_id), int(length), int(k), _ptr(words),
                                   _stream(stream)), "sme_draw_probes")
 
 
 def sme_equilibrate(op, u, v, u_bar, v_bar, *, T, k, t_begin=1, t0=0, seed=0, stream_base=0, alpha=0.0,
                     beta=0.0, gamma=0.0, M=0.0, flags=0, stream=None):
+    """Algorithm 1: T iterations with k probes from the given (u, v, u_bar, v_bar), updated in place."""
     p = sme_equil_params(alpha, beta, gamma, M, int(T), int(k), int(t_begin), int(t0), int(seed), int(stream_base),
                          int(flags))
     _check(load().sme_equilibrate(op, ctypes.byref(p), _ptr(u), _ptr(v), _ptr(u_bar), _ptr(v_bar), _stream(stream)),
@@ -242,15 +249,18 @@ def sme_equilibrate(op, u, v, u_bar, v_bar, *, T, k, t_begin=1, t0=0, seed=0, st
 
 
 def sme_op_check(op, stream=None):
+    """Raise the error recorded in the operator's device status word, if any."""
     _check(load().sme_op_check(op, _stream(stream)), "sme_op_check")
 
 
 def sme_estimate(op, u, v, t, k, seed, stream_base, z_u, z_v, stream=None):
+    """One Section 3.1 estimate of the squared row / column norms of D A E at (u, v) into z_u, z_v."""
     _check(load().sme_estimate(op, _ptr(u), _ptr(v), int(t), int(k), int(seed), int(stream_base), _ptr(z_u),
                                _ptr(z_v), _stream(stream)), "sme_estimate")
 
 
 def sme_evaluate(op, u, v, alpha=0.0, beta=0.0, gamma=0.0, r2=None, c2=None, stream=None) -> dict:
+    """Exact squared row / column norms of D A E (FP64) and the spread, RMS error and objective, as a dict."""
     res = sme_eval_result()
     _check(load().sme_evaluate(op, _ptr(u), _ptr(v), float(alpha), float(beta), float(gamma), _ptr(r2), _ptr(c2),
                                ctypes.byref(res), _stream(stream)), "sme_evaluate")
@@ -311,11 +321,13 @@ def sme_batch_create(mats, dtype=None, stream=None):
 
 
 def sme_batch_destroy(b):
+    """Destroy a batch and its block-diagonal operator."""
     if b:
         _check(load().sme_batch_destroy(b), "sme_batch_destroy")
 
 
 def sme_batch_get_info(b):
+    """(count, row offsets, column offsets) of the matrices in a batch."""
     count = ctypes.c_int32()
     _check(load().sme_batch_get_info(b, ctypes.byref(count), None, None), "sme_batch_get_info")
     ro = np.zeros(count.value + 1, np.int64)
@@ -326,6 +338,7 @@ def sme_batch_get_info(b):
 
 def sme_batch_equilibrate(b, u, v, u_bar, v_bar, *, T, k, t_begin=1, t0=0, seed=0, stream_base=0, alpha=0.0,
                           beta=0.0, gamma=0.0, M=0.0, flags=0, stream=None):
+    """Algorithm 1 for every matrix of a batch at once (per-matrix targets and probe streams)."""
     p = sme_equil_params(alpha, beta, gamma, M, int(T), int(k), int(t_begin), int(t0), int(seed), int(stream_base),
                          int(flags))
     _check(load().sme_batch_equilibrate(b, ctypes.byref(p), _ptr(u), _ptr(v), _ptr(u_bar), _ptr(v_bar),
@@ -333,17 +346,20 @@ def sme_batch_equilibrate(b, u, v, u_bar, v_bar, *, T, k, t_begin=1, t0=0, seed=
 
 
 def sme_batch_estimate(b, u, v, t, k, seed, stream_base, z_u, z_v, stream=None):
+    """One estimate for every matrix of a batch (probe streams stream_base + 2b, + 2b + 1)."""
     _check(load().sme_batch_estimate(b, _ptr(u), _ptr(v), int(t), int(k), int(seed), int(stream_base), _ptr(z_u),
                                      _ptr(z_v), _stream(stream)), "sme_batch_estimate")
 
 
 def sme_batch_op(b):
+    """The batch's block-diagonal operator (owned by the batch), for calls that take an operator."""
     op = ctypes.c_void_p()
     _check(load().sme_batch_op(b, ctypes.byref(op)), "sme_batch_op")
     return op
 
 
 def sme_op_autotune(op, k, stream=None) -> dict:
+    """Time the launch shapes of the iteration kernel for k on this operator and keep the fastest."""
     spc, cf, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
     _check(load().sme_op_autotune(op, int(k), ctypes.byref(spc), ctypes.byref(cf), ctypes.byref(ms), _stream(stream)),
            "sme_op_autotune")
@@ -370,6 +386,7 @@ def _params(T, k, t_begin, t0, seed, stream_base, alpha, beta, gamma, M, flags):
 
 def sme_equilibrate_targets(op, row_targets_sq, col_targets_sq, u, v, u_bar, v_bar, *, T, k, t_begin=1, t0=0, seed=0,
                             stream_base=0, gamma=0.0, M=0.0, flags=0, stream=None):
+    """Section 6 varying norms: squared row / column targets in place of alpha^2, beta^2."""
     p = _params(T, k, t_begin, t0, seed, stream_base, 0.0, 0.0, gamma, M, flags)
     _check(load().sme_equilibrate_targets(op, ctypes.byref(p), _ptr(row_targets_sq), _ptr(col_targets_sq), _ptr(u),
                                           _ptr(v), _ptr(u_bar), _ptr(v_bar), _stream(stream)),
@@ -378,6 +395,7 @@ def sme_equilibrate_targets(op, row_targets_sq, col_targets_sq, u, v, u_bar, v_b
 
 def sme_equilibrate_symmetric(op, u, u_bar, *, T, k, t_begin=1, t0=0, seed=0, stream_base=0, alpha=0.0, gamma=0.0,
                               M=0.0, flags=0, stream=None):
+    """Algorithm 2: one scaling u for a symmetric operator."""
     p = _params(T, k, t_begin, t0, seed, stream_base, alpha, alpha, gamma, M, flags)
     _check(load().sme_equilibrate_symmetric(op, ctypes.byref(p), _ptr(u), _ptr(u_bar), _stream(stream)),
            "sme_equilibrate_symmetric")
@@ -385,6 +403,7 @@ def sme_equilibrate_symmetric(op, u, u_bar, *, T, k, t_begin=1, t0=0, seed=0, st
 
 def sme_equilibrate_block(op, row_block_ptr, col_block_ptr, u, v, u_bar, v_bar, *, T, k, t_begin=1, t0=0, seed=0,
                           stream_base=0, alpha=0.0, beta=0.0, gamma=0.0, M=0.0, flags=0, stream=None):
+    """Section 6 block equilibration: one log-scaling per contiguous row block and column block."""
     rb = np.ascontiguousarray(row_block_ptr, dtype=np.int64)
     cb = np.ascontiguousarray(col_block_ptr, dtype=np.int64)
     p = _params(T, k, t_begin, t0, seed, stream_base, alpha, beta, gamma, M, flags)
@@ -393,21 +412,25 @@ def sme_equilibrate_block(op, row_block_ptr, col_block_ptr, u, v, u_bar, v_bar, 
 
 
 def sme_mlp_create(seed=0):
+    """Create the warm-start network (8 -> 128 -> 128 -> 1) with seeded initial weights."""
     h = ctypes.c_void_p()
     _check(load().sme_mlp_create(ctypes.byref(h), int(seed)), "sme_mlp_create")
     return h
 
 
 def sme_mlp_destroy(mlp):
+    """Destroy a warm-start network."""
     if mlp:
         _check(load().sme_mlp_destroy(mlp), "sme_mlp_destroy")
 
 
 def sme_mlp_param_count() -> int:
+    """Number of FP32 parameters of the warm-start network."""
     return int(load().sme_mlp_param_count())
 
 
 def sme_mlp_get_params(mlp):
+    """(parameters, input normalisation) of a network as NumPy arrays."""
     p = np.zeros(sme_mlp_param_count(), np.float32)
     nrm = np.zeros(16, np.float32)
     _check(load().sme_mlp_get_params(mlp, _ptr(p), _ptr(nrm)), "sme_mlp_get_params")
@@ -415,16 +438,19 @@ def sme_mlp_get_params(mlp):
 
 
 def sme_mlp_set_params(mlp, params=None, norm=None):
+    """Set a network's parameters and / or its input normalisation."""
     p = None if params is None else np.ascontiguousarray(params, np.float32)
     nrm = None if norm is None else np.ascontiguousarray(norm, np.float32)
     _check(load().sme_mlp_set_params(mlp, _ptr(p), _ptr(nrm)), "sme_mlp_set_params")
 
 
 def sme_mlp_forward(mlp, X, y, stream=None):
+    """Network outputs y for the feature rows X (CUDA tensors)."""
     _check(load().sme_mlp_forward(mlp, _ptr(X), int(X.shape[0]), _ptr(y), _stream(stream)), "sme_mlp_forward")
 
 
 def sme_mlp_gradient(mlp, X, target, grad=None, stream=None):
+    """Mean squared-error loss and its gradient for (X, target); returns the loss."""
     loss = ctypes.c_float()
     _check(load().sme_mlp_gradient(mlp, _ptr(X), _ptr(target), int(X.shape[0]), _ptr(grad), ctypes.byref(loss),
                                    _stream(stream)), "sme_mlp_gradient")
@@ -432,6 +458,7 @@ def sme_mlp_gradient(mlp, X, target, grad=None, stream=None):
 
 
 def sme_mlp_train_step(mlp, X, target, lr, stream=None, want_loss=False):
+    """One Adam step on (X, target) with learning rate lr; optionally returns the loss."""
     loss = ctypes.c_float()
     _check(load().sme_mlp_train_step(mlp, _ptr(X), _ptr(target), int(X.shape[0]), float(lr),
                                      ctypes.byref(loss) if want_loss else None, _stream(stream)), "sme_mlp_train_step")
@@ -439,11 +466,13 @@ def sme_mlp_train_step(mlp, X, target, lr, stream=None, want_loss=False):
 
 
 def sme_op_features(op, seed, row_features, col_features, stream=None):
+    """The 8 warm-start features of every row and column of an operator."""
     _check(load().sme_op_features(op, int(seed), _ptr(row_features), _ptr(col_features), _stream(stream)),
            "sme_op_features")
 
 
 def sme_warm_start(op, mlp, seed, u0, v0, stream=None):
+    """u0, v0 = network(features) for an operator."""
     _check(load().sme_warm_start(op, mlp, int(seed), _ptr(u0), _ptr(v0), _stream(stream)), "sme_warm_start")
 
 
@@ -457,16 +486,19 @@ def sme_batch_evaluate(b, u, v, alpha=0.0, beta=0.0, gamma=0.0, stream=None):
 
 
 def sme_batch_features(b, seed, row_features, col_features, stream=None):
+    """The warm-start features of every matrix of a batch."""
     _check(load().sme_batch_features(b, int(seed), _ptr(row_features), _ptr(col_features), _stream(stream)),
            "sme_batch_features")
 
 
 def sme_batch_warm_start(b, mlp, seed, u0, v0, stream=None):
+    """u0, v0 = network(features) for every matrix of a batch."""
     _check(load().sme_batch_warm_start(b, mlp, int(seed), _ptr(u0), _ptr(v0), _stream(stream)),
            "sme_batch_warm_start")
 
 
 def sme_op_norm2(op, u_bar=None, v_bar=None, iters=100, stream=None) -> float:
+    """||D A E||_2 by power iteration (the CCP step sizes of Section 5.2)."""
     out = ctypes.c_double()
     _check(load().sme_op_norm2(op, _ptr(u_bar), _ptr(v_bar), int(iters), ctypes.byref(out), _stream(stream)),
            "sme_op_norm2")
