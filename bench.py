@@ -250,8 +250,8 @@ class ClockSampler:
 
 def run_reference(args, rank, world):
     """The oracle as it stands on the host cores: each step is one full iteration of Algorithm 1 (FP64 C,
-    single-threaded) on the same matrix, resumed from the previous step's state (about 5 s on the GPU machine's
-    host, so the default 20 + 3 steps take about two minutes)."""
+    single-threaded) on the same matrix, resumed from the previous step's state (5-7 s on a Grace core, so
+    the default 20 + 3 steps take two to three minutes)."""
     if rank != 0:
         return 0
     import numpy as np
