@@ -66,9 +66,9 @@ def dense_source_hash():
     h.update(_section(KERNEL_HEADER, b"Philox4x32-10", b"------ operator"))
     return h.hexdigest()
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sgd_iteration_f32_k32_large.txt")
-# Random 8-byte gathers per second from L2-resident tables, measured on GB300 by
-# paper_1602_06621_gb300/microbench/gather_ceiling.cu (profiles/sgd_iteration_f32_k32_large.txt): the second
-# ceiling of the sparse kernels, which gather one table entry per nonzero per pass.
+# Random 8-byte gathers per second from L2-resident tables, measured on GB300 by a random-gather
+# microbenchmark (figures in profiles/sgd_iteration_f32_k32_large.txt): the second ceiling of the sparse
+# kernels, which gather one table entry per nonzero per pass.
 GATHER_CEILING_PER_S = 2.93e11
 
 
@@ -76,7 +76,7 @@ def gather_roofline(nnz, launch_s):
     """The gather ceiling beside the HBM roofline: 2 nnz gathers per iteration (one per pass)."""
     g = 2.0 * nnz
     return {"gathers_per_launch": g, "achieved_per_s": g / launch_s, "peak_per_s": GATHER_CEILING_PER_S,
-            "frac": g / launch_s / GATHER_CEILING_PER_S, "peak_kind": "measured (gather_ceiling.cu)"}
+            "frac": g / launch_s / GATHER_CEILING_PER_S, "peak_kind": "measured (random-gather microbenchmark)"}
 
 
 def parse():

@@ -439,24 +439,31 @@ sme_status sme_batch_warm_start(sme_batch b, sme_mlp mlp, uint64_t seed, void *u
 
 /*
  * sme_estimate_rows_static -- the row-side estimate of sme_estimate (z_u only, FP32),
- * for callers that must not allocate device memory on this path: code recording
- * into a CUDA graph, code whose device memory is already owned by a caching
- * allocator, or a latency-critical loop that cannot take the synchronisation an
- * allocation or a free may cause.  The paper has no counterpart: this is a
- * property of the library, not of the method.
+ * for callers that must not allocate device memory on this path: code whose device
+ * memory is already owned by a caching allocator (a framework pool that reserved the
+ * free memory), a latency-critical loop that cannot take the device-wide
+ * synchronisation an allocation or a free may cause, or a plug-in handed fixed device
+ * buffers by a host application that keeps the memory budget to itself.  The paper
+ * has no counterpart: this is a property of the library, not of the method.
  *
  * Works directly on the caller's device CSR (row_ptr int32[m+1], col_idx int32[nnz],
  * vals float[nnz]) and device vectors u[m], v[n]; writes z_u[m].  Probes as in
  * sme_estimate (iteration t, Philox stream stream_base for s).  k in {1,2,4,...,32}.
  *
  * Calls no cudaMalloc/cudaFree.  Its only scratch, a gather table of n entries,
- * is a fixed array of SME_STATIC_MAX_COLS entries (8 bytes each) inside the
+ * is a fixed array of SME_STATIC_MAX_COLS entries (8 bytes each, 8 MiB) inside the
  * library; every GPU that loads the library holds it until the process exits.
  * n > SME_STATIC_MAX_COLS returns SME_ERR_ARG.  All calls on a device share the
- * array: calls whose GPU work overlaps (unordered streams) race on it.  The first
- * call on each device looks up the array's device address (cudaGetSymbolAddress),
- * so make that first call before beginning any stream capture.  The CSR is not
- * validated here (pass one sme_op_create_csr would accept).
+ * array and it keeps the last call's contents (each call rewrites the n entries it
+ * reads, so nothing needs clearing): calls whose GPU work overlaps (unordered
+ * streams) race on it.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) and keeps it, so make that first call before
+ * beginning any stream capture; a device reset (cudaDeviceReset) invalidates the
+ * kept address, so do not call this entry point again in a process after one.
+ *
+ * The CSR is not validated on the host (row_ptr must be nondecreasing from 0, with
+ * row_ptr[m] entries in col_idx and vals).  A column index outside [0, n) is never
+ * used to address the table: its row is written as NaN, the other rows are exact.
  */
 #define SME_STATIC_MAX_COLS (1 << 20)
 

@@ -1,11 +1,12 @@
 // Allocation-free variant of the row-side norm estimator.
 //
 // Who needs it: code that must not call cudaMalloc/cudaFree on the path where it
-// estimates row norms -- for example a caller that is recording its work into a
-// CUDA graph, one that runs under a caching allocator which already owns all
-// free device memory, or a latency-critical loop that cannot afford the
-// device-wide synchronisation an allocation or a free may imply.  Such a caller
-// passes its own CSR, scalings and output in device memory, and the only
+// estimates row norms -- for example a caller whose device memory is already
+// owned by a caching allocator (a framework pool that reserved the free memory),
+// a latency-critical loop that cannot take the device-wide synchronisation an
+// allocation or a free may imply, or a plug-in that is handed fixed device
+// buffers by a host application that keeps the memory budget to itself.  Such a
+// caller passes its own CSR, scalings and output in device memory, and the only
 // scratch the computation needs (a gather table with one entry per column:
 // e^{v_j} and the probe word of column j) lives in a fixed array inside this
 // library instead of being allocated.
@@ -15,7 +16,8 @@
 // Every call on a device shares it and it keeps the last call's contents; each
 // call rewrites entries [0, n) before reading them, so nothing has to start at
 // zero.  Calls whose work overlaps on the GPU (different streams, no ordering
-// between them) race on the array.
+// between them) race on the array.  A column index outside [0, n) is never used
+// to address the table: the row that holds it gets NaN.
 
 #include <cuda_runtime.h>
 
@@ -66,9 +68,11 @@ __global__ void static_fill_table(int64_t n, const float *v, uint32_t t, uint32_
 }
 
 // One thread per row, straight from the caller's CSR: z_u[i] = e^{2 u_i} (1/k) sum_p (sum_j A_ij e^{v_j} s_jp)^2.
+// A column index outside [0, n) is skipped (it would address a stale entry, or memory past the array) and
+// marks the row: z_u[i] = NaN.
 template <int K>
-__global__ void static_rows(int64_t m, const int32_t *rp, const int32_t *col, const float *val, const float *u,
-                            const uint2 *tab, float *z)
+__global__ void static_rows(int64_t m, int64_t n, const int32_t *rp, const int32_t *col, const float *val,
+                            const float *u, const uint2 *tab, float *z)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
@@ -76,8 +80,14 @@ __global__ void static_rows(int64_t m, const int32_t *rp, const int32_t *col, co
 #pragma unroll
     for (int p = 0; p < K; ++p) P[p] = 0.f;
     float C = 0.f;
+    bool bad = false;
     for (int32_t q = rp[i]; q < rp[i + 1]; ++q) {
-        const uint2 e = tab[col[q]];
+        const uint32_t j = (uint32_t)col[q];
+        if (j >= (uint64_t)n) {
+            bad = true;
+            continue;
+        }
+        const uint2 e = tab[j];
         const float y = val[q] * __uint_as_float(e.x);
         C += y;
 #pragma unroll
@@ -91,7 +101,7 @@ __global__ void static_rows(int64_t m, const int32_t *rp, const int32_t *col, co
         ss += yp * yp;
     }
     const float ex = expf(u[i]);
-    z[i] = ex * ex * ss * (1.f / (float)K);
+    z[i] = bad ? __int_as_float(0x7fc00000) : ex * ex * ss * (1.f / (float)K);
 }
 
 }  // namespace sme
@@ -123,12 +133,12 @@ extern "C" sme_status sme_estimate_rows_static(int64_t m, int64_t n, const int32
                                                                    (uint32_t)seed, (uint32_t)(seed >> 32), tab);
     const unsigned grid = (unsigned)((m + 255) / 256);
     switch (k) {
-        case 1: static_rows<1><<<grid, 256, 0, s>>>(m, row_ptr, col_idx, vals, u, tab, z_u); break;
-        case 2: static_rows<2><<<grid, 256, 0, s>>>(m, row_ptr, col_idx, vals, u, tab, z_u); break;
-        case 4: static_rows<4><<<grid, 256, 0, s>>>(m, row_ptr, col_idx, vals, u, tab, z_u); break;
-        case 8: static_rows<8><<<grid, 256, 0, s>>>(m, row_ptr, col_idx, vals, u, tab, z_u); break;
-        case 16: static_rows<16><<<grid, 256, 0, s>>>(m, row_ptr, col_idx, vals, u, tab, z_u); break;
-        default: static_rows<32><<<grid, 256, 0, s>>>(m, row_ptr, col_idx, vals, u, tab, z_u); break;
+        case 1: static_rows<1><<<grid, 256, 0, s>>>(m, n, row_ptr, col_idx, vals, u, tab, z_u); break;
+        case 2: static_rows<2><<<grid, 256, 0, s>>>(m, n, row_ptr, col_idx, vals, u, tab, z_u); break;
+        case 4: static_rows<4><<<grid, 256, 0, s>>>(m, n, row_ptr, col_idx, vals, u, tab, z_u); break;
+        case 8: static_rows<8><<<grid, 256, 0, s>>>(m, n, row_ptr, col_idx, vals, u, tab, z_u); break;
+        case 16: static_rows<16><<<grid, 256, 0, s>>>(m, n, row_ptr, col_idx, vals, u, tab, z_u); break;
+        default: static_rows<32><<<grid, 256, 0, s>>>(m, n, row_ptr, col_idx, vals, u, tab, z_u); break;
     }
     SME_CUDA(cudaGetLastError());
     return SME_OK;

@@ -18,7 +18,7 @@ __all__ = [
     "SmeError", "load", "SME_F64", "SME_F32", "SME_BF16", "SME_FP8E4M3", "SME_EQ_ASYNC", "SME_EQ_NO_GRAPH", "SME_EQ_TIMED",
     "sme_op_create_csr", "sme_op_create_dense", "sme_op_destroy", "sme_op_get_info", "sme_draw_probes",
     "sme_equilibrate", "sme_op_check", "sme_estimate", "sme_evaluate", "sme_lsqr", "sme_status_string",
-    "default_params", "sme_estimate_rows_static", "SME_STATIC_MAX_COLS", "sme_batch_create", "sme_batch_destroy",
+    "sme_estimate_rows_static", "SME_STATIC_MAX_COLS", "sme_batch_create", "sme_batch_destroy",
     "sme_batch_get_info", "sme_batch_equilibrate", "sme_batch_estimate", "sme_batch_op", "sme_op_autotune", "sme_batch_lsqr",
     "sme_equilibrate_targets", "sme_equilibrate_symmetric", "sme_equilibrate_block", "sme_mlp_create",
     "sme_mlp_destroy", "sme_mlp_param_count", "sme_mlp_get_params", "sme_mlp_set_params", "sme_mlp_forward",
@@ -182,12 +182,6 @@ def sme_release_cached_memory() -> None:
     _check(load().sme_release_cached_memory(), "sme_release_cached_memory")
 
 
-def default_params(m: int, n: int) -> dict:
-    """Section 4 parameters: alpha=(n/m)^(1/4), beta=(m/n)^(1/4), gamma=0.1, M=log(1e4)."""
-    import math
-    return dict(alpha=(n / m) ** 0.25, beta=(m / n) ** 0.25, gamma=0.1, M=math.log(1e4))
-
-
 def sme_op_create_csr(m, n, row_ptr, col_idx, vals, dtype=None, stream=None):
     """Create a sparse operator.  Host NumPy arrays are copied; CUDA tensors are read in place."""
     on_device = not isinstance(row_ptr, np.ndarray)
@@ -287,8 +281,33 @@ def sme_lsqr(op, u_bar, v_bar, b, x, *, tol=1e-6, max_iters=100000, check_every=
     return out
 
 
+def _check_static_args(m, n, row_ptr, col_idx, vals, u, v, z_u):
+    """The C side sees raw pointers only: check dtypes, device, contiguity and lengths here."""
+    import torch
+
+    named = dict(row_ptr=(row_ptr, torch.int32, m + 1), col_idx=(col_idx, torch.int32, None),
+                 vals=(vals, torch.float32, None), u=(u, torch.float32, m), v=(v, torch.float32, n),
+                 z_u=(z_u, torch.float32, m))
+    devices = set()
+    for name, (x, dt, length) in named.items():
+        if not isinstance(x, torch.Tensor) or not x.is_cuda:
+            raise SmeError(-1, "sme_estimate_rows_static", f"{name} must be a CUDA tensor")
+        if x.dtype != dt:
+            raise SmeError(-1, "sme_estimate_rows_static", f"{name} must be {dt}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise SmeError(-1, "sme_estimate_rows_static", f"{name} must be contiguous")
+        if length is not None and x.numel() != length:
+            raise SmeError(-1, "sme_estimate_rows_static", f"{name} has {x.numel()} elements, expected {length}")
+        devices.add(x.device)
+    if col_idx.numel() != vals.numel():
+        raise SmeError(-1, "sme_estimate_rows_static", "col_idx and vals differ in length")
+    if len(devices) != 1:
+        raise SmeError(-1, "sme_estimate_rows_static", "arguments on more than one device")
+
+
 def sme_estimate_rows_static(m, n, row_ptr, col_idx, vals, u, v, t, k, seed, stream_base, z_u, stream=None):
     """Row estimate without any device allocation (see include/sme.h); all arguments are CUDA tensors."""
+    _check_static_args(int(m), int(n), row_ptr, col_idx, vals, u, v, z_u)
     _check(load().sme_estimate_rows_static(int(m), int(n), _ptr(row_ptr), _ptr(col_idx), _ptr(vals), _ptr(u), _ptr(v),
                                            int(t), int(k), int(seed), int(stream_base), _ptr(z_u), _stream(stream)),
            "sme_estimate_rows_static")
