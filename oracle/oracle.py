@@ -24,17 +24,18 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .build import build_oracle
+from .build import build_oracle, build_oracle_omp
 
 __all__ = [
     "lib", "philox4x32_10", "probe_signs", "row_estimate", "col_estimate", "psgd_step", "equilibrate",
     "psgd_step_sampled", "exact_norms_sq", "csr_matvec", "dense_estimate_sampled", "psgd_step_targets",
     "psgd_step_symmetric", "block_step", "default_params", "objective", "gradient",
     "rms_error", "spread", "log_phi", "kappa", "sinkhorn_knopp", "block_minimize_u", "block_minimize_v",
-    "regularized_optimum", "lsqr", "LsqrResult", "OracleCSR",
+    "regularized_optimum", "lsqr", "LsqrResult", "OracleCSR", "set_parallel", "threads",
 ]
 
-_LIB = None
+_LIBS = {}
+_PARALLEL = False
 _dp = ctypes.POINTER(ctypes.c_double)
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -42,10 +43,24 @@ _u32p = ctypes.POINTER(ctypes.c_uint32)
 _i64, _i32, _u64, _u32, _d = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double
 
 
+def set_parallel(enabled: bool) -> int:
+    """Route later calls to the OpenMP build of the oracle (True: all host cores, or OMP_NUM_THREADS) or to the
+    single-threaded checker build (False, the default).  Both give the same bits.  Returns the thread count."""
+    global _PARALLEL
+    _PARALLEL = bool(enabled)
+    return threads()
+
+
+def threads() -> int:
+    """Threads the active build runs its parallel loops on (1 for the checker build)."""
+    return int(lib().or_max_threads())
+
+
 def lib():
-    global _LIB
-    if _LIB is None:
-        L = ctypes.CDLL(build_oracle())
+    key = "omp" if _PARALLEL else "plain"
+    if key not in _LIBS:
+        L = ctypes.CDLL(build_oracle_omp() if _PARALLEL else build_oracle())
+        L.or_max_threads.restype = ctypes.c_int
         L.or_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
         L.or_probe_sign.argtypes = [_u64, _u32, _u32, _u32, _u32]
         L.or_probe_sign.restype = _d
@@ -68,8 +83,8 @@ def lib():
         L.or_csr_matvec.argtypes = [_i64, _i64p, _i32p, _dp, _dp, _dp]
         L.or_dense_estimate_sampled.argtypes = [_i64, _i64, ctypes.POINTER(ctypes.c_float), _dp, _dp, _dp, _i32, _i32,
                                                 _u64, _i32, _i64, _i64p, _i64, _i64p, _dp, _dp]
-        _LIB = L
-    return _LIB
+        _LIBS[key] = L
+    return _LIBS[key]
 
 
 def _p(a, t):

@@ -36,6 +36,27 @@
 #include <stdlib.h>
 #include <string.h>
 
+/*
+ * Threads.  The checker build is single-threaded; a second build of this same file with OpenMP times the
+ * oracle on all host cores.  The parallel loops only split independent outputs between threads (rows,
+ * columns, probe-table entries): every sum is still taken in the order written, so both builds give the
+ * same bits.
+ */
+#ifdef _OPENMP
+#include <omp.h>
+#define OR_PARALLEL_FOR _Pragma("omp parallel for schedule(static)")
+static int or_thread_count(void) { return omp_get_num_threads(); }
+static int or_thread_id(void) { return omp_get_thread_num(); }
+#define OR_PARALLEL _Pragma("omp parallel")
+int or_max_threads(void) { return omp_get_max_threads(); }
+#else
+#define OR_PARALLEL_FOR
+#define OR_PARALLEL
+static int or_thread_count(void) { return 1; }
+static int or_thread_id(void) { return 0; }
+int or_max_threads(void) { return 1; }
+#endif
+
 /* ---------------------------------------------------------------- Philox */
 
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
@@ -81,6 +102,7 @@ double or_probe_sign(uint64_t seed, uint32_t index, uint32_t t, uint32_t stream,
 /* sgn[idx * k + p] for idx in [0, len), p in [0, k). */
 void or_draw_probes(uint64_t seed, int32_t t, int32_t stream, int64_t len, int32_t k, double *sgn)
 {
+    OR_PARALLEL_FOR
     for (int64_t idx = 0; idx < len; ++idx)
         for (int32_t p = 0; p < k; ++p)
             sgn[idx * k + p] = or_probe_sign(seed, (uint32_t)idx, (uint32_t)t, (uint32_t)stream, (uint32_t)p);
@@ -93,6 +115,7 @@ void or_row_estimate(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t
                      const double *u, const double *v, const double *s, int32_t k, double *z)
 {
     (void)n;
+    OR_PARALLEL_FOR
     for (int64_t i = 0; i < m; ++i) {
         double acc = 0.0;
         for (int32_t p = 0; p < k; ++p) {
@@ -108,18 +131,27 @@ void or_row_estimate(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t
     }
 }
 
-/* z[j] = (1/k) sum_p ((E A^T D w_p)_j)^2; w is m x k.  Accumulated by scattering over the CSR. */
+/* z[j] = (1/k) sum_p ((E A^T D w_p)_j)^2; w is m x k.  Accumulated by scattering over the CSR, rows in
+ * order.  With several threads, each owns a contiguous range of columns and scatters only into those. */
 void or_col_estimate(int64_t m, int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
                      const double *u, const double *v, const double *w, int32_t k, double *z)
 {
     double *y = (double *)calloc((size_t)(n * k), sizeof(double));
-    for (int64_t i = 0; i < m; ++i)
-        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            int64_t j = col[e];
-            double b = exp(v[j]) * val[e] * exp(u[i]);
-            for (int32_t p = 0; p < k; ++p)
-                y[j * k + p] += b * w[i * k + p];
-        }
+    OR_PARALLEL
+    {
+        const int64_t nt = or_thread_count(), id = or_thread_id();
+        const int64_t j0 = n * id / nt, j1 = n * (id + 1) / nt;
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                int64_t j = col[e];
+                if (j < j0 || j >= j1)
+                    continue;
+                double b = exp(v[j]) * val[e] * exp(u[i]);
+                for (int32_t p = 0; p < k; ++p)
+                    y[j * k + p] += b * w[i * k + p];
+            }
+    }
+    OR_PARALLEL_FOR
     for (int64_t j = 0; j < n; ++j) {
         double acc = 0.0;
         for (int32_t p = 0; p < k; ++p)
@@ -150,12 +182,14 @@ void or_psgd_step_targets(int64_t m, int64_t n, const int64_t *row_ptr, const in
     or_row_estimate(m, n, row_ptr, col, val, u, v, s, k, zu);
     or_col_estimate(m, n, row_ptr, col, val, u, v, w, k, zv);
     double eta = 2.0 / (gamma * ((double)t + (double)t0 + 1.0));
+    OR_PARALLEL_FOR
     for (int64_t i = 0; i < m; ++i) {
         double target = rt ? rt[i] : alpha * alpha;
         double un = clip(u[i] - eta * (zu[i] - target + gamma * u[i]), -M, M);
         u[i] = un;
         ubar[i] = 2.0 * un / ((double)t + 2.0) + (double)t * ubar[i] / ((double)t + 2.0);
     }
+    OR_PARALLEL_FOR
     for (int64_t j = 0; j < n; ++j) {
         double target = ct ? ct[j] : beta * beta;
         double vn = clip(v[j] - eta * (zv[j] - target + gamma * v[j]), -M, M);
@@ -363,8 +397,9 @@ void or_dense_estimate_sampled(int64_t m, int64_t n, const float *A, const doubl
     double *w = (double *)malloc((size_t)(m * k) * sizeof(double));
     or_draw_probes(seed, t, stream_base, n, k, s);
     or_draw_probes(seed, t, stream_base + 1, m, k, w);
-    double *y = (double *)malloc((size_t)k * sizeof(double));
+    OR_PARALLEL_FOR
     for (int64_t q = 0; q < n_rows; ++q) {
+        double *y = (double *)malloc((size_t)k * sizeof(double));
         int64_t i = rows[q];
         double ci = row_scale ? row_scale[i] : 1.0;
         for (int32_t p = 0; p < k; ++p)
@@ -378,8 +413,11 @@ void or_dense_estimate_sampled(int64_t m, int64_t n, const float *A, const doubl
         for (int32_t p = 0; p < k; ++p)
             acc += y[p] * y[p];
         zu[q] = acc / (double)k;
+        free(y);
     }
+    OR_PARALLEL_FOR
     for (int64_t q = 0; q < n_cols; ++q) {
+        double *y = (double *)malloc((size_t)k * sizeof(double));
         int64_t j = cols[q];
         for (int32_t p = 0; p < k; ++p)
             y[p] = 0.0;
@@ -393,8 +431,8 @@ void or_dense_estimate_sampled(int64_t m, int64_t n, const float *A, const doubl
         for (int32_t p = 0; p < k; ++p)
             acc += y[p] * y[p];
         zv[q] = acc / (double)k;
+        free(y);
     }
-    free(y);
     free(s);
     free(w);
 }

@@ -163,3 +163,31 @@ def test_spread_of_equilibrated_matrix_is_one():
     A = 3.0 * np.eye(6)[[2, 0, 5, 1, 4, 3]]
     r2, c2 = O.exact_norms_sq(A, np.zeros(6), np.zeros(6))
     assert O.spread(r2, c2) == (1.0, 1.0)
+
+
+# ------------------------------------------------------------------ the OpenMP build of the same source
+
+def test_openmp_build_gives_the_checker_bits():
+    """The timed CPU baseline runs an OpenMP build of the oracle; it must compute exactly what the checker does."""
+    import os
+    import subprocess
+    import sys
+
+    code = r"""
+import numpy as np, oracle as O
+from paper_1602_06621_gb300 import inputs as I
+A = O.OracleCSR.from_any(I.workload_large(scale=0.003, seed=9))
+out = []
+for par in (False, True):
+    O.set_parallel(par)
+    st = O.equilibrate(A, T=3, k=8, seed=2)
+    out.append(np.concatenate(st))
+print(O.threads(), int(np.array_equal(out[0], out[1])))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="4")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    nthreads, same = map(int, r.stdout.split())
+    assert nthreads == 4
+    assert same == 1
