@@ -32,6 +32,7 @@
 #include <mutex>
 
 #include "sme_internal.cuh"
+#include "tc_common.cuh"
 
 namespace sme {
 
@@ -54,102 +55,7 @@ struct DenseCfg {
 static_assert(DenseCfg<256>::BYTES + 1024 <= 227 * 1024 && DenseCfg<128>::BYTES + 1024 <= 227 * 1024,
               "dense rings exceed the shared memory of one CTA");
 constexpr int DN_THREADS = 192;      // warp 0 TMA, warp 1 MMA + TMEM owner, warps 2..5 epilogue
-constexpr uint32_t DN_WAIT_LIMIT = 1u << 22;  // polls of a try_wait before a wait is abandoned
 
-struct DenseOp {
-    bool fp8 = false;
-    int64_t m = 0, n = 0;
-    // A (m x n) and A^T (n x m) in K-blocked order: the 128 x 64 block (row tile t, K-block kb) is one
-    // contiguous 16 KB run at ((t * cols/64 + kb) * 128) * 64 elements, rows of 64 inside it.
-    __nv_bfloat16 *A = nullptr, *At = nullptr;
-    float *row_scale = nullptr;                 // FP8 input: per-row scales (applied in the epilogue)
-    __nv_bfloat16 *Bf[2] = {nullptr, nullptr};  // [2k][n]: forward operand (columns' scale x probes)
-    __nv_bfloat16 *Bb[2] = {nullptr, nullptr};  // [2k][m]: backward operand
-    int kcap = 0;
-    float *x[2] = {nullptr, nullptr}, *xb[2] = {nullptr, nullptr};  // u, ubar / v, vbar
-    CUtensorMap mapA, mapAt, mapBf[2], mapBb[2];
-};
-
-// ------------------------------------------------------------------ PTX helpers
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for phase `parity` of `bar`; false if it did not complete within the limit.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
-{
-    for (uint32_t i = 0; i < DN_WAIT_LIMIT; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-// Shared-memory address, in the cluster window, of the same variable in CTA `rank` of the cluster.
-__device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank)
-{
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
-    return r;
-}
-
-// Copy into this CTA's shared memory whose completion is counted on an mbarrier of either CTA of the
-// pair (`bar_cluster`: a cluster-window address).
-__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, int x, int y, uint32_t bar_cluster)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar_cluster)
-        : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-// All threads of every CTA of the cluster.
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc_sw128_u32(uint32_t saddr)
-{
-    const uint64_t addr = saddr;
-    uint64_t d = 0;
-    d |= (addr >> 4) & 0x3FFFull;              // start address
-    d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)((8 * DN_ROWB) >> 4) << 32; // stride byte offset: 8 rows x 128 bytes
-    d |= (uint64_t)1 << 46;                    // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;                    // swizzle mode: 128 bytes
-    return d;
-}
 
 // Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
@@ -165,31 +71,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-
-// Arrives on the mbarrier at `bar`'s offset in every CTA of `mask` once this thread's MMAs have completed.
-__device__ __forceinline__ void mma_commit_multicast(uint64_t *bar, uint16_t mask)
-{
-    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                     smem_u32(bar)),
-                 "h"(mask)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
-{
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // ------------------------------------------------------------------ the iteration kernel
@@ -460,24 +341,6 @@ __global__ void transpose_bf16(const __nv_bfloat16 *in, int64_t rows, int64_t co
     }
 }
 
-// FP8 (e4m3) input -> BF16.  Every e4m3 value is exactly representable in BF16 (3 of its 7 mantissa
-// bits, exponents -9..8), so the tensor-core operand is the FP8 matrix itself; row scales stay separate.
-__global__ void fp8_to_bf16(const uint8_t *in, int64_t m, int64_t n, int64_t lda, __nv_bfloat16 *out)
-{
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= m * n) return;
-    const int64_t i = idx / n, j = idx % n;
-    const uint8_t b = in[i * lda + j];
-    // e4m3: 1 sign, 4 exponent (bias 7), 3 mantissa; 0x7f / 0xff are NaN.
-    const int s = b >> 7, e = (b >> 3) & 15, f = b & 7;
-    float v;
-    if ((b & 0x7f) == 0x7f) v = NAN;
-    else if (e == 0) v = ldexpf((float)f, -9);
-    else v = ldexpf((float)(8 + f), e - 10);
-    if (s) v = -v;
-    out[idx] = __float2bfloat16_rn(v);
-}
-
 __global__ void bf16_check_finite(const __nv_bfloat16 *a, int64_t count, int *status)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
@@ -486,45 +349,10 @@ __global__ void bf16_check_finite(const __nv_bfloat16 *a, int64_t count, int *st
 
 // ------------------------------------------------------------------ host side
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn encode_fn()
-{
-    static EncodeTiledFn fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-    });
-    return fn;
-}
-
 // Row-major BF16 matrix (rows x cols) viewed with boxes of DN_BK columns (128 bytes) x box_rows rows.
 static sme_status make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int box_rows)
 {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) {
-        set_error("cuTensorMapEncodeTiled unavailable");
-        return SME_ERR_CUDA;
-    }
-    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)DN_BK, (cuuint32_t)box_rows};
-    const cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
-        return SME_ERR_CUDA;
-    }
-    return SME_OK;
+    return tc_make_map(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, base, rows, cols, 2, DN_BK, box_rows);
 }
 
 // K-blocked matrix (rows x cols) viewed as (rows * cols / 64) rows of 64 elements, boxes of 128 such rows:
@@ -624,13 +452,24 @@ static DenseArgs dense_base(sme_op op, double alpha, double beta, double gamma, 
     return a;
 }
 
+// E4M3 storage (dense_f8.cu).
+sme_status dense_f8_create(sme_op op, const uint8_t *src, int64_t lda, cudaStream_t s);
+sme_status dense_f8_finish_create(sme_op op, cudaStream_t s);
+sme_status dense_f8_equilibrate(sme_op op, const sme_equil_params *p, double alpha, double beta, double gamma,
+                                double M, float *u, float *v, float *ub, float *vb, cudaStream_t s);
+sme_status dense_f8_estimate(sme_op op, const float *u, const float *v, int t, int k, uint64_t seed, int sb,
+                             double alpha, double beta, double gamma, double M, float *zu, float *zv, cudaStream_t s);
+sme_status dense_f8_exact_norms(sme_op op, const double *sq_u, const double *sq_v, double *r2, double *c2,
+                                cudaStream_t s);
+
 void dense_destroy(sme_op op)
 {
     DenseOp *D = op->dense;
     if (!D) return;
     for (void *p : {(void *)D->A, (void *)D->At, (void *)D->row_scale, (void *)D->Bf[0], (void *)D->Bf[1],
                     (void *)D->Bb[0], (void *)D->Bb[1], (void *)D->x[0], (void *)D->x[1], (void *)D->xb[0],
-                    (void *)D->xb[1]})
+                    (void *)D->xb[1], (void *)D->A8, (void *)D->At8, (void *)D->Bf8[0], (void *)D->Bf8[1],
+                    (void *)D->Bb8[0], (void *)D->Bb8[1], (void *)D->f8_small})
         dev_release(p);
     delete D;
     op->dense = nullptr;
@@ -652,10 +491,11 @@ sme_status dense_equilibrate(sme_op op, const sme_equil_params *p, float *u, flo
         set_error("dense operators support k = 128 or 256");
         return SME_ERR_UNSUPPORTED;
     }
-    SME_TRY(ensure_dense_workspace(op, kp));
-    DenseOp *D = op->dense;
     double alpha = p->alpha, beta = p->beta, gamma = p->gamma, M = p->M;
     resolve_params(op, alpha, beta, gamma, M);
+    if (op->dense->fp8) return dense_f8_equilibrate(op, p, alpha, beta, gamma, M, u, v, ub, vb, s);
+    SME_TRY(ensure_dense_workspace(op, kp));
+    DenseOp *D = op->dense;
     const uint32_t sid_s = (uint32_t)p->stream_base, sid_w = sid_s + 1u;
     const int tb = p->t_begin;
     SME_CUDA(cudaMemcpyAsync(D->x[0], u, D->m * 4, cudaMemcpyDeviceToDevice, s));
@@ -740,6 +580,7 @@ sme_status dense_exact_norms(sme_op op, const float *u, const float *v, double *
     const int64_t m = D->m, n = D->n;
     dense_sq<<<nblk(m), 256, 0, s>>>(m, u, D->row_scale, sq_u);
     dense_sq<<<nblk(n), 256, 0, s>>>(n, v, nullptr, sq_v);
+    if (D->fp8) return dense_f8_exact_norms(op, sq_u, sq_v, r2, c2, s);
     dense_row_norms<<<nblk(m * 32), 256, 0, s>>>(D->A, m, n, sq_v, sq_u, r2);
     dense_row_norms<<<nblk(n * 32), 256, 0, s>>>(D->At, n, m, sq_u, sq_v, c2);
     SME_CUDA(cudaGetLastError());
@@ -752,6 +593,11 @@ sme_status dense_estimate(sme_op op, const float *u, const float *v, int t, int 
     if (k != 128 && k != 256) {
         set_error("dense operators support k = 128 or 256");
         return SME_ERR_UNSUPPORTED;
+    }
+    if (op->dense->fp8) {
+        double alpha = 0, beta = 0, gamma = 0, M = 0;
+        resolve_params(op, alpha, beta, gamma, M);
+        return dense_f8_estimate(op, u, v, t, k, seed, sb, alpha, beta, gamma, M, zu, zv, s);
     }
     SME_TRY(ensure_dense_workspace(op, k));
     DenseOp *D = op->dense;
@@ -815,13 +661,51 @@ extern "C" sme_status sme_op_create_dense(sme_op *out, int64_t m, int64_t n, con
         return e;
     };
     if ((st = dev_alloc(op, (void **)&op->d_status, sizeof(int))) != SME_OK) return fail(st);
+    if (cudaMemsetAsync(op->d_status, 0, sizeof(int), s) != cudaSuccess) return fail(SME_ERR_CUDA);
+    if (D->fp8) {
+        // E4M3 codes stay E4M3: staged densely (pitch n) on the device, then blocked into A and A^T.
+        void *staging = nullptr;
+        if (cudaMalloc(&staging, (size_t)m * n) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SME_ERR_OOM);
+        }
+        auto done = [&](sme_status e) {
+            cudaStreamSynchronize(s);
+            cudaFree(staging);
+            return e == SME_OK ? e : fail(e);
+        };
+        if (cudaMemcpy2DAsync(staging, (size_t)n, A, (size_t)lda, (size_t)n, (size_t)m,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return done(SME_ERR_CUDA);
+        if (row_scales) {
+            if ((st = dev_alloc(op, (void **)&D->row_scale, (size_t)m * 4)) != SME_OK) return done(st);
+            if (cudaMemcpyAsync(D->row_scale, row_scales, (size_t)m * 4,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s) != cudaSuccess)
+                return done(SME_ERR_CUDA);
+        }
+        if ((st = dense_f8_create(op, (const uint8_t *)staging, n, s)) != SME_OK) return done(st);
+        int st8 = 0;
+        cudaMemcpyAsync(&st8, op->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaError_t e8 = cudaStreamSynchronize(s);
+        if (e8 != cudaSuccess) {
+            cuda_fail(e8, "sme_op_create_dense", __LINE__);
+            return done(SME_ERR_CUDA);
+        }
+        if (st8 & ST_BAD_VALUE) {
+            set_error("sme_op_create_dense: NaN code or non-finite row scale");
+            return done(SME_ERR_NONFINITE);
+        }
+        if ((st = dense_f8_finish_create(op, s)) != SME_OK) return done(st);
+        done(SME_OK);
+        *out = op;
+        return SME_OK;
+    }
     if ((st = dev_alloc(op, (void **)&D->A, (size_t)m * n * 2)) != SME_OK) return fail(st);
     if ((st = dev_alloc(op, (void **)&D->At, (size_t)m * n * 2)) != SME_OK) return fail(st);
-    if (cudaMemsetAsync(op->d_status, 0, sizeof(int), s) != cudaSuccess) return fail(SME_ERR_CUDA);
-    const size_t esz = D->fp8 ? 1 : 2;
+    const size_t esz = 2;
     const void *src = A;
     void *staging = nullptr;
-    if (!on_device || lda != n || D->fp8) {
+    if (!on_device || lda != n) {
         // Stage the input densely on the device (copy from host, or repack a strided device matrix).
         if (cudaMalloc(&staging, (size_t)m * lda * esz) != cudaSuccess) {
             cudaGetLastError();
@@ -834,17 +718,7 @@ extern "C" sme_status sme_op_create_dense(sme_op *out, int64_t m, int64_t n, con
         }
         src = staging;
     }
-    if (D->fp8) {
-        if (row_scales) {
-            if ((st = dev_alloc(op, (void **)&D->row_scale, (size_t)m * 4)) != SME_OK) {
-                cudaFree(staging);
-                return fail(st);
-            }
-            cudaMemcpyAsync(D->row_scale, row_scales, (size_t)m * 4,
-                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
-        }
-        fp8_to_bf16<<<nblk(m * n), 256, 0, s>>>((const uint8_t *)src, m, n, lda, D->A);
-    } else if (lda != n) {
+    if (lda != n) {
         cudaMemcpy2DAsync(D->A, (size_t)n * 2, src, (size_t)lda * 2, (size_t)n * 2, (size_t)m, cudaMemcpyDeviceToDevice,
                           s);
     } else {

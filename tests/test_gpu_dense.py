@@ -114,27 +114,186 @@ def _e4m3_values():
     return vals
 
 
-def test_dense_fp8_with_row_scales_matches_oracle():
+# ------------------------------------------------------------------ E4M3 storage and operands
+#
+# On an E4M3 operator the matrix stays E4M3 (A_ij = c_i q_ij) and each B operand is one E4M3 term,
+# e4m3(2^S e^{x_j} c_j) s_jp, with a power-of-two S per operand.  Inside E4M3's normal range rounding
+# y 2^S gives 2^S times y rounded to 4 significant bits (round to nearest, ties to even), whatever S is, so
+# the scalings the tensor cores see are round4(e^{x_j} c_j).  The oracle is given exactly those (through
+# the probe signs s_jp round4(e^{x_j} c_j) / (e^{x_j} c_j)), and then only FP32 accumulation separates the
+# two: the bound _tol(K) above applies.  Against the exact scalings each estimate also carries the E4M3
+# rounding of the scalings, at most 2^-4 relative per scaling: E_s[dz_i] = sum_j x_ij^2 (2 eps_j + eps_j^2),
+# at most (2^-3 + 2^-8) r2_i, plus a zero-mean part whose standard deviation is below sqrt(2/k) times that;
+# _F8_ROUNDING_BOUND = 0.19 covers both with five standard deviations at k = 128.
+
+_F8_ROUNDING_BOUND = 0.19
+
+
+def _round4(x):
+    """Round to 4 significant bits, ties to even: E4M3 rounding inside its normal range."""
+    x = np.asarray(x, np.float64)
+    f, e = np.frexp(x)
+    return np.ldexp(np.rint(f * 16.0) / 16.0, e)
+
+
+def _e4m3_matrix(m, n, seed, var=1.5):
+    """A badly scaled matrix quantised as the bench does: row i as E4M3 codes of A_i / c_i, c_i = max|A_i| / 448."""
     import torch
-    m, n, k = 256, 256, 256
-    rng = np.random.default_rng(11)
-    codes = rng.integers(0, 256, size=(m, n)).astype(np.uint8)
-    codes[(codes & 0x7F) == 0x7F] = 0x38  # no NaN codes (0x38 is 1.0)
-    scales = np.exp(rng.normal(0, 1.5, m)).astype(np.float32)
-    table = _e4m3_values()
-    Af = table[codes].astype(np.float32)  # exact
-    op = sme.sme_op_create_dense(m, n, torch.tensor(codes, device="cuda"), dtype=sme.SME_FP8E4M3,
-                                 row_scales=torch.tensor(scales, device="cuda"))
+    A = I.dense_badly_scaled(m, n, seed, var=var).astype(np.float32)
+    scales = (np.abs(A).max(axis=1) / 448.0).astype(np.float32)
+    q = torch.tensor(A / scales[:, None]).to(torch.float8_e4m3fn)
+    codes = q.view(torch.uint8).numpy().copy()
+    codes[(codes & 0x7F) == 0x7F] = 0x38
+    Af = _e4m3_values()[codes]  # exact E4M3 values
+    return codes, scales, Af
+
+
+def _fp8_op(codes, scales):
+    import torch
+    m, n = codes.shape
+    return sme.sme_op_create_dense(m, n, torch.tensor(codes, device="cuda"), dtype=sme.SME_FP8E4M3,
+                                   row_scales=torch.tensor(scales, device="cuda"))
+
+
+def _rounded_signs(seed, t, stream, x, c, k):
+    """Probe signs times round4(e^{x} c) / (e^{x} c): the oracle's estimate then sees the rounded scalings."""
+    sc = np.exp(np.asarray(x, np.float64)) * (1.0 if c is None else np.asarray(c, np.float64))
+    sc32 = np.exp(np.asarray(x, np.float32)).astype(np.float64) * (1.0 if c is None else np.asarray(c, np.float64))
+    ratio = _round4(sc32) / sc
+    return O.probe_signs(seed, t, stream, len(x), k) * ratio[:, None]
+
+
+@pytest.mark.parametrize("m,n", [(256, 256), (384, 256), (1280, 384), (384, 2560)])
+@pytest.mark.parametrize("k", [128, 256])
+def test_dense_fp8_representable_scalings_match_oracle(m, n, k):
+    """Scalings chosen so that e^{v_j} and e^{u_i} c_i are E4M3 values: the operands are exact, so the E4M3
+    path must match the oracle on the dequantised matrix within the FP32 accumulation bound."""
+    codes, scales, Af = _e4m3_matrix(m, n, seed=m + n + k)
+    rng = np.random.default_rng(k + 1)
+    grid = _e4m3_values()[0x20:0x58]  # normal values 2^-3 .. 2^3 (codes 0x20 .. 0x57)
+    qv = rng.choice(grid, n)
+    qu = rng.choice(grid, m)
+    v = np.log(qv).astype(np.float32)
+    u = np.log(qu / scales.astype(np.float64)).astype(np.float32)
+    op = _fp8_op(codes, scales)
     try:
-        u = rng.normal(0, 0.5, m).astype(np.float32)
-        v = rng.normal(0, 0.5, n).astype(np.float32)
-        zu, zv = _gpu_estimate(op, m, n, u, v, t=2, k=k, seed=9)
+        zu, zv = _gpu_estimate(op, m, n, u, v, t=3, k=k, seed=7)
     finally:
         sme.sme_op_destroy(op)
-    ezu, ezv = O.dense_estimate_sampled(Af, u, v, np.arange(m), np.arange(n), t=2, k=k, seed=9, row_scale=scales)
+    ezu, ezv = O.dense_estimate_sampled(Af.astype(np.float32), u, v, np.arange(m), np.arange(n), t=3, k=k, seed=7,
+                                        row_scale=scales)
     r2, c2 = _exact_sq(Af, u.astype(np.float64), v.astype(np.float64), row_scale=scales)
-    assert np.all(np.abs(zu - ezu) <= _tol(n) * r2)
-    assert np.all(np.abs(zv - ezv) <= _tol(m) * c2)
+    assert np.all(np.abs(zu - ezu) <= _tol(n) * r2), np.max(np.abs(zu - ezu) / r2)
+    assert np.all(np.abs(zv - ezv) <= _tol(m) * c2), np.max(np.abs(zv - ezv) / c2)
+
+
+@pytest.mark.parametrize("m,n,k", [(256, 384, 256), (1280, 384, 128), (1280, 384, 256)])
+def test_dense_fp8_estimate_equals_oracle_on_rounded_scalings(m, n, k):
+    """Random scalings: equal to the oracle given the E4M3-rounded scalings (FP32 accumulation bound), and
+    within _F8_ROUNDING_BOUND r2 of the oracle given the exact ones."""
+    codes, scales, Af = _e4m3_matrix(m, n, seed=2 * m + n)
+    rng = np.random.default_rng(5)
+    u = rng.normal(0, 0.5, m).astype(np.float32)
+    v = rng.normal(0, 0.5, n).astype(np.float32)
+    t, seed = 4, 11
+    op = _fp8_op(codes, scales)
+    try:
+        zu, zv = _gpu_estimate(op, m, n, u, v, t=t, k=k, seed=seed)
+    finally:
+        sme.sme_op_destroy(op)
+    A64 = O.OracleCSR.from_any(Af * scales.astype(np.float64)[:, None])
+    u64, v64 = u.astype(np.float64), v.astype(np.float64)
+    r2, c2 = _exact_sq(Af, u64, v64, row_scale=scales)
+    s_r = _rounded_signs(seed, t, 0, v, None, k)
+    w_r = _rounded_signs(seed, t, 1, u, scales, k)
+    rzu = O.row_estimate(A64, u64, v64, s_r)
+    rzv = O.col_estimate(A64, u64, v64, w_r)
+    assert np.all(np.abs(zu - rzu) <= _tol(n) * r2), np.max(np.abs(zu - rzu) / r2)
+    assert np.all(np.abs(zv - rzv) <= _tol(m) * c2), np.max(np.abs(zv - rzv) / c2)
+    ezu = O.row_estimate(A64, u64, v64, O.probe_signs(seed, t, 0, n, k))
+    ezv = O.col_estimate(A64, u64, v64, O.probe_signs(seed, t, 1, m, k))
+    assert np.all(np.abs(zu - ezu) <= _F8_ROUNDING_BOUND * r2), np.max(np.abs(zu - ezu) / r2)
+    assert np.all(np.abs(zv - ezv) <= _F8_ROUNDING_BOUND * c2), np.max(np.abs(zv - ezv) / c2)
+
+
+def test_dense_fp8_every_step_matches_oracle_on_rounded_scalings():
+    """20 iterations of Algorithm 1 on an E4M3 operator (k = 256, step offset t0 = 100 so that the scalings
+    stay inside E4M3's normal range), each step against the oracle's step from the GPU's own state with the
+    E4M3-rounded scalings in its estimates (norm-wise relative error of [u; v; ubar; vbar] <= 1e-4).  This
+    covers the operand scale exponents chosen from the step bound and the ring of per-iteration maxima."""
+    import torch
+    m, n, k, t0 = 1280, 384, 256, 100
+    codes, scales, Af = _e4m3_matrix(m, n, seed=8, var=0.5)
+    Aeff = Af * scales.astype(np.float64)[:, None]
+    A64 = O.OracleCSR.from_any(Aeff)
+    d = O.default_params(m, n)
+    # Warm start: one sweep of row then column normalisation of |A|^2 towards alpha^2, beta^2 (the averages
+    # start at the start point), so that the steps are small from the first one.
+    u0 = -0.5 * np.log((Aeff ** 2).sum(1) / d["alpha"] ** 2)
+    v0 = -0.5 * np.log(((Aeff ** 2) * np.exp(2 * u0)[:, None]).sum(0) / d["beta"] ** 2)
+    u0, v0 = u0.astype(np.float32).astype(np.float64), v0.astype(np.float32).astype(np.float64)
+    start = (u0, v0, u0.copy(), v0.copy())
+    op = _fp8_op(codes, scales)
+    worst = 0.0
+    state = start
+    try:
+        for t in range(1, 21):
+            g = [torch.tensor(x, dtype=torch.float32, device="cuda") for x in state]
+            sme.sme_equilibrate(op, *g, T=1, k=k, seed=3, t_begin=t, t0=t0)
+            got = [x.cpu().double().numpy() for x in g]
+            # Each operand (its own scale exponent) stays inside the normal range below its scaled maximum.
+            for sc in (np.exp(state[0]) * scales, np.exp(state[1])):
+                assert sc.max() / sc.min() < 2.0 ** 12
+            s_r = _rounded_signs(3, t, 0, state[1].astype(np.float32), None, k)
+            w_r = _rounded_signs(3, t, 1, state[0].astype(np.float32), scales, k)
+            ref = O.psgd_step(A64, *state, s_r, w_r, t, t0=t0, **d)
+            a = np.concatenate(got)
+            b = np.concatenate(ref)
+            worst = max(worst, np.linalg.norm(a - b) / np.linalg.norm(b))
+            state = tuple(got)
+        # One 20-iteration call equals the step-by-step run (the scale exponents follow from the state).
+        g = [torch.tensor(x, dtype=torch.float32, device="cuda") for x in start]
+        sme.sme_equilibrate(op, *g, T=20, k=k, seed=3, t0=t0)
+        for x, y in zip(g, state):
+            np.testing.assert_array_equal(x.cpu().double().numpy(), y)
+    finally:
+        sme.sme_op_destroy(op)
+    assert worst <= 1e-4, worst
+
+
+def test_dense_fp8_whole_run_outcome_close_to_oracle():
+    """Whole run from the zero start (paper's step, T = 60, k = 256) on a 256 x 384 E4M3 operator: the
+    first steps move the scalings across E4M3's whole range, so the run is compared by its outcome with the
+    oracle's run on the dequantised matrix.
+
+    The single E4M3 term biases the fixed point: a row's expected estimate is sum_j x_ij^2 (1 + eps_j)^2 with
+    |eps_j| <= 2^-4, so where the exact method settles at r2_i = alpha^2 - gamma u_i the E4M3 path settles at
+    r2_i times a factor in [(1 + 2^-4)^-2, (1 - 2^-4)^-2]: each norm moves by at most (1 +- 2^-4)^-1, and the
+    spread (a ratio of two norms) by at most (1 + 2^-4) / (1 - 2^-4) = 1.133.  Bound asserted: that factor
+    times 1.05 for the finite run; the averaged scalings within 5 % norm-wise."""
+    import torch
+    m, n, k, T = 256, 384, 256, 60
+    codes, scales, Af = _e4m3_matrix(m, n, seed=13)
+    A64 = O.OracleCSR.from_any(Af * scales.astype(np.float64)[:, None])
+    op = _fp8_op(codes, scales)
+    try:
+        g = [torch.zeros(x, device="cuda") for x in (m, n, m, n)]
+        sme.sme_equilibrate(op, *g, T=T, k=k, seed=1)
+        got = [x.cpu().double().numpy() for x in g]
+    finally:
+        sme.sme_op_destroy(op)
+    O.set_parallel(True)  # the OpenMP build of the oracle: the checker's bits on every host core
+    try:
+        ref = O.equilibrate(A64, T=T, k=k, seed=1)
+    finally:
+        O.set_parallel(False)
+    ub = np.concatenate(got[2:])
+    rb = np.concatenate(ref[2:])
+    assert np.linalg.norm(ub - rb) / np.linalg.norm(rb) <= 0.05
+    sg = max(O.spread(*O.exact_norms_sq(A64, got[2], got[3])))
+    so = max(O.spread(*O.exact_norms_sq(A64, ref[2], ref[3])))
+    bias = (1 + 2.0 ** -4) / (1 - 2.0 ** -4)
+    assert so / (1.05 * bias) <= sg <= so * 1.05 * bias, (sg, so)
 
 
 def test_dense_full_size_sampled_estimate():
@@ -163,6 +322,40 @@ def test_dense_full_size_sampled_estimate():
     assert np.all(np.abs(zu[rows] - ezu) <= _tol(n) * r2), np.max(np.abs(zu[rows] - ezu) / r2)
     assert np.all(np.abs(zv[cols] - ezv) <= _tol(m) * c2), np.max(np.abs(zv[cols] - ezv) / c2)
     assert np.all(np.isfinite(zu)) and np.all(np.isfinite(zv))
+
+
+def test_dense_fp8_full_size_sampled_estimate():
+    """16384 x 16384 E4M3 with per-row scales (the dense workload's quantisation), k = 256: 24 sampled rows and
+    24 columns of one estimate against the oracle given the E4M3-rounded scalings (rows: u and round4(e^{v});
+    columns: round4(e^{u} c) and v), within the FP32 accumulation bound; and within _F8_ROUNDING_BOUND r2 of
+    the oracle given the exact scalings."""
+    m = n = 16384
+    codes, scales, Af = _e4m3_matrix(m, n, seed=3)
+    op = _fp8_op(codes, scales)
+    try:
+        rng = np.random.default_rng(0)
+        u = rng.normal(0, 0.5, m).astype(np.float32)
+        v = rng.normal(0, 0.5, n).astype(np.float32)
+        zu, zv = _gpu_estimate(op, m, n, u, v, t=1, k=256, seed=0)
+    finally:
+        sme.sme_op_destroy(op)
+    assert np.all(np.isfinite(zu)) and np.all(np.isfinite(zv))
+    rows = np.sort(rng.choice(m, 24, replace=False))
+    cols = np.sort(rng.choice(n, 24, replace=False))
+    u64, v64 = u.astype(np.float64), v.astype(np.float64)
+    c64 = scales.astype(np.float64)
+    v_r = np.log(_round4(np.exp(v).astype(np.float64)))
+    u_r = np.log(_round4(np.exp(u).astype(np.float64) * c64) / c64)
+    Af32 = Af.astype(np.float32)
+    rzu, _ = O.dense_estimate_sampled(Af32, u64, v_r, rows, [], t=1, k=256, seed=0, row_scale=c64)
+    _, rzv = O.dense_estimate_sampled(Af32, u_r, v64, [], cols, t=1, k=256, seed=0, row_scale=c64)
+    ezu, ezv = O.dense_estimate_sampled(Af32, u64, v64, rows, cols, t=1, k=256, seed=0, row_scale=c64)
+    r2 = np.array([np.sum((np.exp(u64[i]) * c64[i] * Af[i] * np.exp(v64)) ** 2) for i in rows])
+    c2 = np.array([np.sum((np.exp(u64) * c64 * Af[:, j] * np.exp(v64[j])) ** 2) for j in cols])
+    assert np.all(np.abs(zu[rows] - rzu) <= _tol(n) * r2), np.max(np.abs(zu[rows] - rzu) / r2)
+    assert np.all(np.abs(zv[cols] - rzv) <= _tol(m) * c2), np.max(np.abs(zv[cols] - rzv) / c2)
+    assert np.all(np.abs(zu[rows] - ezu) <= _F8_ROUNDING_BOUND * r2)
+    assert np.all(np.abs(zv[cols] - ezv) <= _F8_ROUNDING_BOUND * c2)
 
 
 def test_dense_argument_errors():
