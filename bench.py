@@ -58,11 +58,27 @@ DENSE_SOURCE = os.path.join(ROOT, "paper_1602_06621_gb300", "csrc", "dense.cu")
 DENSE_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dense_iteration_bf16_k256.txt")
 
 
+TC_HEADER = os.path.join(ROOT, "paper_1602_06621_gb300", "csrc", "tc_common.cuh")
+DENSE_F8_SOURCE = os.path.join(ROOT, "paper_1602_06621_gb300", "csrc", "dense_f8.cu")
+DENSE_F8_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dense_iteration_f8_k256.txt")
+
+
 def dense_source_hash():
-    """Hash of the dense iteration kernel's device code in dense.cu (configuration, PTX helpers, the kernel),
-    and the Philox section of the internal header."""
+    """Hash of the BF16 dense iteration kernel's device code: dense.cu from its configuration to the kernel's
+    end, the shared tensor-core helpers (tc_common.cuh) and the Philox section of the internal header."""
     h = hashlib.sha256()
     h.update(_section(DENSE_SOURCE, b"constexpr int DN_BM", b"// Operand of iteration t from a state vector"))
+    h.update(open(TC_HEADER, "rb").read())
+    h.update(_section(KERNEL_HEADER, b"Philox4x32-10", b"------ operator"))
+    return h.hexdigest()
+
+
+def dense_f8_source_hash():
+    """Hash of the E4M3 dense iteration kernel's device code: dense_f8.cu up to its set-up kernels, the shared
+    tensor-core helpers and the Philox section of the internal header."""
+    h = hashlib.sha256()
+    h.update(_section(DENSE_F8_SOURCE, b"constexpr int F8_BM", b"// ------------------------------------------------------------------ set-up kernels"))
+    h.update(open(TC_HEADER, "rb").read())
     h.update(_section(KERNEL_HEADER, b"Philox4x32-10", b"------ operator"))
     return h.hexdigest()
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sgd_iteration_f32_k32_large.txt")
@@ -91,6 +107,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lsqr", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="default workload only: leave out the dense and batched results carried on its line")
+    ap.add_argument("--dense-dtypes", default="bf16,fp8",
+                    help="dense workload: which storages to run (bf16, fp8 or both, comma-separated)")
     ap.add_argument("--plain-cap", type=int, default=20000,
                     help="iteration cap of the plain-LSQR comparison (min(200 n, 1e6) is the long reading)")
     ap.add_argument("--workload", choices=["large", "dense", "batched", "learned", "ccp", "lsqr"], default="large",
@@ -303,8 +323,10 @@ def fp8_summary(N, k, T, steps, f8, bf, peaks, kind):
     flops = 2 * 2.0 * N * N * k
     f8_peak = 2.0 * float(peaks.get("bf16_tflops", peaks.get("bf16_tflops_sustained")))
     achieved = bytes_iter / f8["iter_s"] / 1e9
-    d = np.concatenate([f8["ub"], f8["vb"]]).astype(np.float64) - np.concatenate([bf["ub"], bf["vb"]])
-    rel = float(np.linalg.norm(d) / np.linalg.norm(np.concatenate([bf["ub"], bf["vb"]])))
+    rel = None
+    if bf is not None:
+        d = np.concatenate([f8["ub"], f8["vb"]]).astype(np.float64) - np.concatenate([bf["ub"], bf["vb"]])
+        rel = float(np.linalg.norm(d) / np.linalg.norm(np.concatenate([bf["ub"], bf["vb"]])))
     return {"storage": "E4M3 codes + per-row FP32 scales, kept E4M3 in HBM (A and A^T)",
             "operands": "single E4M3 term per scaling (relative rounding <= 2^-4), tcgen05.mma kind::f8f6f4",
             "launch_us": f8["iter_s"] * 1e6, "probe_pairs_per_s": k * T * steps / f8["elapsed"],
@@ -320,11 +342,19 @@ def fp8_summary(N, k, T, steps, f8, bf, peaks, kind):
 
 
 def run_dense(args, rank, world, local):
+    line = dense_line(args, rank, world, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def dense_line(args, rank, world, local):
     """T iterations of Algorithm 1 on a dense 16384^2 matrix (N(0,1) entries, row and column factors of
     variance 1.5), k = 256 probes per iteration, on the tensor cores: stored in BF16 (the line's value), and
     as FP8-E4M3 with per-row scales (reported beside it).  For each, the norm spread of the result on the
     stored matrix (library evaluation) and on the FP64 matrix (NumPy), and a CPU baseline: the FP64 oracle's
-    estimate for a sample of rows and columns at the final state, with the GPU's error on that sample."""
+    estimate for a sample of rows and columns at the final state, with the GPU's error on that sample.
+    --dense-dtypes fp8 runs the E4M3 storage alone (then the line's value is the E4M3 run's)."""
     import numpy as np
     import torch
 
@@ -392,10 +422,29 @@ def run_dense(args, rank, world, local):
                 "spread_stored_matrix": max(q["row_spread"], q["col_spread"]), "rms_stored_matrix": q["rms"],
                 "spread_fp64_matrix": spread(r2, c2)}
 
-    op = sme.sme_op_create_dense(N, N, Ab, dtype=sme.SME_BF16)
-    bf = run(op)
-    op8 = sme.sme_op_create_dense(N, N, codes, dtype=sme.SME_FP8E4M3, row_scales=scales)
-    f8 = run(op8)
+    dtypes = [x.strip() for x in args.dense_dtypes.split(",") if x.strip()]
+    op = op8 = bf = f8 = None
+    if "bf16" in dtypes:
+        op = sme.sme_op_create_dense(N, N, Ab, dtype=sme.SME_BF16)
+        bf = run(op)
+    if "fp8" in dtypes:
+        op8 = sme.sme_op_create_dense(N, N, codes, dtype=sme.SME_FP8E4M3, row_scales=scales)
+        f8 = run(op8)
+    if bf is None:
+        # E4M3 alone: the line reports the E4M3 run.
+        line = {
+            "metric": METRIC, "value": world * k * T * args.steps / f8["elapsed"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * f8["elapsed"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "e4m3", "data": "synthetic",
+            "config": {"workload": f"dense tensor-core path: A {N}x{N} FP8-E4M3 with per-row scales, entries "
+                                   f"N(0,1)*exp(N(0,1.5)) row and column factors; k={k} +-1 probes (single-term E4M3 "
+                                   f"scalings), FP32 accumulation; T={T}", "m": N, "n": N, "k": k, "T": T},
+            "fp8": fp8_summary(N, k, T, args.steps, f8, None, peaks, kind),
+            "gpu_launches": (T + 4) * args.steps, "clocks": f8["clocks"]}
+        line["roofline"] = dict(line["fp8"]["roofline"],
+                                traffic=recorded_traffic(DENSE_F8_TRAFFIC_FILE, dense_f8_source_hash))
+        sme.sme_op_destroy(op8)
+        return line
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -434,26 +483,44 @@ def run_dense(args, rank, world, local):
                                f"column factors; k={k} +-1 probes (two-term BF16 scalings), FP32 accumulation; T={T}",
                    "m": N, "n": N, "k": k, "T": T, "l2": "inputs larger than L2 (A: 512 MB)"},
         "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
-                     "traffic": recorded_traffic(DENSE_TRAFFIC_FILE, dense_source_hash), "peak_kind": kind + " (bf16 sustained)",
+                     "traffic": recorded_traffic(DENSE_TRAFFIC_FILE, dense_source_hash),
+                     "traffic_kind": "ncu DRAM bytes of one full-size launch (profiles/dense_iteration_bf16_k256.txt)",
+                     "peak_kind": kind + " (bf16 sustained)",
                      "kernel": "dense_iteration<256> (one iteration, both products)",
                      "algorithmic_flops_per_launch": flops, "executed_flops_per_launch": 2 * flops,
                      "launch_us": bf["iter_s"] * 1e6, "hbm_gbs": 2 * 2.0 * N * N / bf["iter_s"] / 1e9},
         "cpu_baseline": cpu,
         "quality": {"spread_stored_matrix": bf["spread_stored_matrix"], "spread_fp64_matrix": bf["spread_fp64_matrix"],
                     "rms_stored_matrix": bf["rms_stored_matrix"]},
-        "fp8": fp8_summary(N, k, T, args.steps, f8, bf, peaks, kind),
-        "gpu_launches": 2 * (T + 2) * args.steps, "clocks": bf["clocks"],
+        "fp8": fp8_summary(N, k, T, args.steps, f8, bf, peaks, kind) if f8 else None,
+        "gpu_launches": (T + 2) * args.steps + ((T + 4) * args.steps if f8 else 0), "clocks": bf["clocks"],
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    if line["fp8"]:
+        line["fp8"]["roofline"]["traffic"] = recorded_traffic(DENSE_F8_TRAFFIC_FILE, dense_f8_source_hash)
     sme.sme_op_destroy(op)
-    sme.sme_op_destroy(op8)
-    return 0
+    if op8 is not None:
+        sme.sme_op_destroy(op8)
+    return line
 
 
 # ------------------------------------------------------------------------------------------ batched workload
 
+def batched_family_for(args, rank):
+    """The batched workload's matrices (generated in spawned processes)."""
+    from paper_1602_06621_gb300 import inputs as I
+
+    m_hi = max(2000, int(2e5 * args.scale))
+    return I.batched_family(512, 1000, m_hi, seed=40 + rank, workers=min(16, os.cpu_count() or 1))
+
+
 def run_batched(args, rank, world, local):
+    line = batched_line(args, rank, world, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def batched_line(args, rank, world, local, mats=None):
     """T iterations of Algorithm 1 (k = 16) on 512 sparse matrices at once: m log-uniform in
     [1e3, 2e5 * scale], n = m U[0.3, 1], 5-50 nonzeros per row, FP32, factors of variance 2."""
     import numpy as np
@@ -466,7 +533,8 @@ def run_batched(args, rank, world, local):
 
     k, T, count = 16, (args.T if args.T != 500 else 300), 512
     m_hi = max(2000, int(2e5 * args.scale))
-    mats = I.batched_family(count, 1000, m_hi, seed=40 + rank, workers=min(16, os.cpu_count() or 1))
+    if mats is None:
+        mats = batched_family_for(args, rank)
     torch.cuda.set_device(local)
     b = sme.sme_batch_create(mats)
     _, ro, co = sme.sme_batch_get_info(b)
@@ -539,10 +607,8 @@ def run_batched(args, rank, world, local):
                     "rms_median": float(np.median([e["rms"] for e in ev]))},
         "lsqr": lsqr,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     sme.sme_batch_destroy(b)
-    return 0
+    return line
 
 
 # ------------------------------------------------------------------------------------------ our arm
@@ -866,6 +932,28 @@ def run_lsqr_paper(args, rank, world, local):
     return 0
 
 
+def secondary_lines(args, rank, world, local, batched_mats):
+    """The dense (BF16 and FP8-E4M3) and batched workloads at their full sizes, each with its own timed region,
+    roofline and clock record (5 timed steps after 3 warm-up steps; the batched per-matrix LSQR is left to
+    --workload batched)."""
+    import copy
+    import gc
+
+    sub = copy.copy(args)
+    sub.steps, sub.warmup, sub.T = min(args.steps, 5), max(3, min(args.warmup, 3)), 500
+    keep = ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "dtype", "config", "roofline", "clocks",
+            "gpu_launches", "quality", "fp8", "cpu_baseline")
+    out = {}
+    d = dense_line(sub, rank, world, local)
+    out["dense"] = {key: d[key] for key in keep if key in d}
+    gc.collect()
+    sub_b = copy.copy(sub)
+    sub_b.no_lsqr = True
+    bl = batched_line(sub_b, rank, world, local, mats=batched_mats)
+    out["batched"] = {key: bl[key] for key in keep if key in bl}
+    return out
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -885,6 +973,12 @@ def main():
         return run_lsqr_paper(args, rank, world, local)
 
     import numpy as np
+
+    # The dense and batched workloads ride on the default line (one GPU only); the batched family is drawn
+    # in spawned processes before this process touches the GPU.
+    secondary = world == 1 and not args.no_secondary
+    batched_mats = batched_family_for(args, rank) if secondary else None
+
     import torch
 
     from paper_1602_06621_gb300 import inputs as I
@@ -1051,6 +1145,8 @@ def main():
                               "col_spread": quality["col_spread"], "rms": quality["rms"],
                               "objective": quality["objective"]},
         }
+        if secondary:
+            line["secondary"] = secondary_lines(args, rank, world, local, batched_mats)
         if lsqr_res:
             last = lsqr_res[-1]
             eq_ms = statistics.median(phase_ms["equilibrate"])
