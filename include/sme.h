@@ -435,6 +435,58 @@ sme_status sme_warm_start(sme_op op, sme_mlp mlp, uint64_t seed, void *u0, void 
 sme_status sme_batch_features(sme_batch b, uint64_t seed, float *row_features, float *col_features, void *stream);
 sme_status sme_batch_warm_start(sme_batch b, sme_mlp mlp, uint64_t seed, void *u0, void *v0, void *stream);
 
+/* ------------------------------------------------------------------ one matrix split over several devices */
+
+/*
+ * Algorithm 1 on one matrix split over P devices (one process per device).  Rows and columns are cut
+ * into P contiguous blocks, block q = [len q / P, len (q + 1) / P).  Part p holds row block p of A (its
+ * forward products, Section 3.1: z_u of its rows) and column block p of A^T (z_v of its columns), and
+ * nothing else of the matrix.  Every iteration of Algorithm 1 needs both estimates at the previous iterate
+ * (u^{t-1}, v^{t-1}): a part's rows read e^{v_j} and the probe signs s_j of EVERY column, its columns read
+ * e^{u_i} and w_i of every row.  These live in two gather tables that each part writes for its own rows
+ * and columns and that the caller all-gathers between iterations (the one exchange of the method: m + n
+ * entries per iteration; probe signs are counter-based, so none are exchanged).
+ *
+ * Tables: the row table has P * row_chunk entries, the column table P * col_chunk, of entry_bytes each
+ * (sme_shard_get_info); part q writes entries [q * chunk, (q + 1) * chunk) (its block's rows in the
+ * library's internal order, the rest of the chunk unused), so an in-place all-gather of equal chunks
+ * assembles them.  The caller owns the tables (device memory) and keeps two of each, for the current and
+ * the next iteration.  A run:
+ *     sme_shard_begin (writes this part's chunks of the tables of iteration t_begin)
+ *     all-gather both tables
+ *     for t = t_begin .. t_begin + T - 1:
+ *         sme_shard_step(t, current tables -> this part's chunks of the next tables); all-gather the next tables
+ *     sme_shard_end
+ * Each part draws exactly the probes an unsplit run draws (probe counters use the whole matrix's index), so
+ * the parts' results together equal the unsplit sme_equilibrate's (bit for bit where no row is long enough
+ * for the kernel to share it among warps; otherwise up to the order of the sums).
+ */
+typedef struct {
+    int32_t parts, part;
+    int64_t m, n;                    /* the whole matrix */
+    int64_t row_begin, row_end;      /* this part's rows [row_begin, row_end) */
+    int64_t col_begin, col_end;      /* this part's columns */
+    int64_t row_chunk, col_chunk;    /* table entries per part */
+    int32_t entry_bytes;             /* bytes per table entry for the k given to sme_shard_get_info */
+} sme_shard_info;
+
+/* Part `part` of `parts` of the CSR matrix (the whole matrix is passed; host or device as in
+ * sme_op_create_csr, SME_F64 or SME_F32).  1 <= parts <= min(m, n).  The op refuses the whole-matrix calls
+ * (sme_equilibrate, sme_estimate, sme_lsqr, ...: SME_ERR_UNSUPPORTED) and runs only sme_shard_*. */
+sme_status sme_op_create_csr_shard(sme_op *out, int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr,
+                                   const int32_t *col_idx, const void *vals, sme_dtype dtype, int on_device,
+                                   int32_t parts, int32_t part, void *stream);
+sme_status sme_shard_get_info(sme_op op, int32_t k, sme_shard_info *info);
+/* u[row_end - row_begin], u_bar (this part's rows, in row order), v[col_end - col_begin], v_bar: the start
+ * state (state type); p as for sme_equilibrate (alpha, beta default from the whole matrix's m, n). */
+sme_status sme_shard_begin(sme_op op, const sme_equil_params *p, const void *u, const void *v, const void *u_bar,
+                           const void *v_bar, void *row_table, void *col_table, void *stream);
+/* Iteration t: reads the whole current tables, writes this part's chunks of the next ones (other buffers). */
+sme_status sme_shard_step(sme_op op, const sme_equil_params *p, int32_t t, const void *row_table_in,
+                          const void *col_table_in, void *row_table_out, void *col_table_out, void *stream);
+/* This part's u, v, u_bar, v_bar after the last step. */
+sme_status sme_shard_end(sme_op op, void *u, void *v, void *u_bar, void *v_bar, void *stream);
+
 /* ------------------------------------------------------------------ allocation-free estimator */
 
 /*

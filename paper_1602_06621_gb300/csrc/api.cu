@@ -396,6 +396,7 @@ extern "C" sme_status sme_op_destroy(sme_op op)
     if (op->graph.exec) cudaGraphExecDestroy(op->graph.exec);
     if (op->graph.stream) cudaStreamDestroy(op->graph.stream);
     if (op->dense) dense_destroy(op);
+    delete op->shard;
     if (op->batch) {
         for (int side = 0; side < 2; ++side)
             for (void *p : {(void *)op->batch->mid[side], (void *)op->batch->loc[side], op->batch->tgt2[side]})
@@ -419,10 +420,46 @@ extern "C" sme_status sme_op_create_csr(sme_op *out, int64_t m, int64_t n, int64
     return create_csr_grouped(out, m, n, nnz, row_ptr, col_idx, vals, dtype, on_device, stream, nullptr, nullptr, 0);
 }
 
+extern "C" sme_status sme_op_create_csr_shard(sme_op *out, int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr,
+                                              const int32_t *col_idx, const void *vals, sme_dtype dtype, int on_device,
+                                              int32_t parts, int32_t part, void *stream)
+{
+    if (parts < 1 || part < 0 || part >= parts || parts > m || parts > n) {
+        if (out) *out = nullptr;
+        set_error("sme_op_create_csr_shard: need 1 <= parts <= min(m, n) and 0 <= part < parts");
+        return SME_ERR_ARG;
+    }
+    return create_csr_grouped(out, m, n, nnz, row_ptr, col_idx, vals, dtype, on_device, stream, nullptr, nullptr, 0,
+                              parts, part);
+}
+
+extern "C" sme_status sme_shard_get_info(sme_op op, int32_t k, sme_shard_info *info)
+{
+    if (!op || !info || k < 1) return SME_ERR_ARG;
+    if (!op->shard) {
+        set_error("sme_shard_get_info: the operator is not a part of a split matrix");
+        return SME_ERR_ARG;
+    }
+    const ShardInfo &I = *op->shard;
+    info->parts = I.parts;
+    info->part = I.part;
+    info->m = I.gm;
+    info->n = I.gn;
+    info->row_begin = I.r0;
+    info->row_end = I.r1;
+    info->col_begin = I.c0;
+    info->col_end = I.c1;
+    info->row_chunk = I.rchunk;
+    info->col_chunk = I.cchunk;
+    // Gather-table entries: {e^x, probe words}, 8 bytes for FP32 state with k <= 32, 16 otherwise.
+    info->entry_bytes = (!op->dbl && k <= 32) ? 8 : 16;
+    return SME_OK;
+}
+
 sme_status sme::create_csr_grouped(sme_op *out, int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr,
                                    const int32_t *col_idx, const void *vals, sme_dtype dtype, int on_device,
                                    void *stream, const uint32_t *row_group_host, const uint32_t *col_group_host,
-                                   int group_bits)
+                                   int group_bits, int32_t shard_parts, int32_t shard_part)
 {
     NvtxRange range("sme build");
     if (!out) return SME_ERR_ARG;
@@ -453,6 +490,21 @@ sme_status sme::create_csr_grouped(sme_op *out, int64_t m, int64_t n, int64_t nn
     op->nnz = nnz;
     op->dtype = dtype;
     op->dbl = dtype == SME_F64;
+    if (shard_parts > 0) {
+        ShardInfo *I = new ShardInfo();
+        I->parts = shard_parts;
+        I->part = shard_part;
+        I->gm = m;
+        I->gn = n;
+        I->gnnz = nnz;
+        I->r0 = m * shard_part / shard_parts;
+        I->r1 = m * (shard_part + 1) / shard_parts;
+        I->c0 = n * shard_part / shard_parts;
+        I->c1 = n * (shard_part + 1) / shard_parts;
+        I->rchunk = (m + shard_parts - 1) / shard_parts;
+        I->cchunk = (n + shard_parts - 1) / shard_parts;
+        op->shard = I;
+    }
     sme_status st = dev_alloc(op, (void **)&op->d_status, sizeof(int));
     if (st != SME_OK) {
         sme_op_destroy(op);
@@ -501,7 +553,13 @@ sme_status sme::create_csr_grouped(sme_op *out, int64_t m, int64_t n, int64_t nn
             cudaMemcpyAsync(groups[i], src[i], (size_t)len[i] * 4, cudaMemcpyHostToDevice, s);
         }
     }
-    st = build_sparse(op, d_rp, d_col, d_val, s, groups[0], groups[1], groups[0] && groups[1] ? group_bits : 0);
+    if (op->shard) {
+        st = build_shard(op, m, n, nnz, d_rp, d_col, d_val, s);
+        op->m = op->shard->r1 - op->shard->r0;
+        op->n = op->shard->c1 - op->shard->c0;
+    } else {
+        st = build_sparse(op, d_rp, d_col, d_val, s, groups[0], groups[1], groups[0] && groups[1] ? group_bits : 0);
+    }
     cudaStreamSynchronize(s);
     for (void *p : tmp) cache_retire(p);  // the copies and the build that read them have completed
     for (void *p : groups)

@@ -517,6 +517,176 @@ static sme_status build_sparse_t(sme_op op, const int32_t *rp, const int32_t *co
     return SME_OK;
 }
 
+// ------------------------------------------------------------------ one part of a split matrix
+
+// Block of each index: block q holds [len q / parts, len (q + 1) / parts), so block(i) = ((i + 1) parts - 1) / len.
+__global__ void block_ids(int64_t len, int32_t parts, uint32_t *blk)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) blk[i] = (uint32_t)(((i + 1) * (int64_t)parts - 1) / len);
+}
+
+// Global table position of every index: its block's chunk plus its rank inside the block (the block-major,
+// descending-length order `iperm`, whose block q starts at q's first index).
+__global__ void global_positions(int64_t len, int32_t parts, int64_t chunk, const int32_t *iperm, int32_t *gpos)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    const int64_t q = ((i + 1) * (int64_t)parts - 1) / len;
+    const int64_t start = len * q / parts;
+    gpos[i] = (int32_t)(q * chunk + (iperm[i] - start));
+}
+
+// The part's rows of the block-major order: perm[r] = order[base + r] (original indices), their lengths and
+// the local inverse (iperm[perm[r] - base] = r).
+__global__ void sub_order(int64_t rows, int64_t base, const int32_t *order, const int32_t *len_orig, int32_t *perm,
+                          int32_t *iperm, int32_t *len_sorted)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const int32_t i = order[base + r];
+    perm[r] = i;
+    iperm[i - base] = (int32_t)r;
+    len_sorted[r] = len_orig[i];
+}
+
+// Block-major, descending-length (stable) order of `len` indices: order[p] = original index at position p, and
+// its inverse.  Every block's indices form one contiguous range of positions starting at the block's first index.
+static sme_status block_major_order(int64_t len, int32_t parts, const int32_t *lens, int32_t *order, int32_t *inv,
+                                    cudaStream_t s)
+{
+    AsyncScratch s_max(s), s_blk(s), s_k0(s), s_k1(s), s_v1(s), s_ls(s);
+    SME_CUDA(s_max.alloc(sizeof(int)));
+    int *d_max = s_max.as<int>();
+    SME_CUDA(cudaMemsetAsync(d_max, 0, sizeof(int), s));
+    max_i32<<<152 * 4, 256, 0, s>>>(lens, len, d_max);
+    int maxlen = 0;
+    SME_CUDA(cudaMemcpyAsync(&maxlen, d_max, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SME_CUDA(cudaStreamSynchronize(s));
+    const int len_bits = std::max(1, bit_length((uint64_t)maxlen));
+    const int blk_bits = std::max(1, bit_length((uint64_t)(parts - 1)));
+    if (len_bits + blk_bits > 32) {
+        set_error("split matrix: row length and part count exceed a 32-bit sort key");
+        return SME_ERR_UNSUPPORTED;
+    }
+    SME_CUDA(s_blk.alloc(len * sizeof(uint32_t)));
+    SME_CUDA(s_k0.alloc(len * sizeof(uint32_t)));
+    SME_CUDA(s_k1.alloc(len * sizeof(uint32_t)));
+    SME_CUDA(s_v1.alloc(len * sizeof(int32_t)));
+    SME_CUDA(s_ls.alloc(len * sizeof(int32_t)));
+    uint32_t *blk = s_blk.as<uint32_t>(), *k0 = s_k0.as<uint32_t>(), *k1 = s_k1.as<uint32_t>();
+    int32_t *v1 = s_v1.as<int32_t>();
+    block_ids<<<nblk(len), 256, 0, s>>>(len, parts, blk);
+    length_keys<<<nblk(len), 256, 0, s>>>(lens, len, maxlen, blk, len_bits, k0, order);
+    bool alt = false;
+    SME_TRY(radix_sort_pairs(k0, order, k1, v1, len, len_bits + blk_bits, s, &alt));
+    if (alt) SME_CUDA(cudaMemcpyAsync(order, v1, len * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    invert_perm<<<nblk(len), 256, 0, s>>>(order, len, inv, lens, s_ls.as<int32_t>());
+    SME_CUDA(cudaGetLastError());
+    return SME_OK;
+}
+
+// Sliced-ELL copy of rows [base, base + rows) of a block-major order.
+template <typename real>
+static sme_status make_sell_part(sme_op op, Sell &S, int64_t rows, int64_t base, const int32_t *order,
+                                 const int32_t *len_orig, cudaStream_t s)
+{
+    S.rows = rows;
+    S.nslices = (rows + 31) / 32;
+    SME_TRY(dev_alloc(op, (void **)&S.perm, rows * sizeof(int32_t)));
+    SME_TRY(dev_alloc(op, (void **)&S.iperm, rows * sizeof(int32_t)));
+    SME_TRY(dev_alloc(op, (void **)&S.len, S.nslices * 32 * sizeof(int32_t)));
+    SME_TRY(dev_alloc(op, (void **)&S.slice_w, S.nslices * sizeof(int32_t)));
+    SME_TRY(dev_alloc(op, (void **)&S.slice_off, (S.nslices + 1) * sizeof(int64_t)));
+    SME_CUDA(cudaMemsetAsync(S.len, 0, S.nslices * 32 * sizeof(int32_t), s));
+    sub_order<<<nblk(rows), 256, 0, s>>>(rows, base, order, len_orig, S.perm, S.iperm, S.len);
+    AsyncScratch s_sl(s);
+    SME_CUDA(s_sl.alloc(S.nslices * sizeof(int64_t)));
+    slice_sizes<<<nblk(S.nslices), 256, 0, s>>>(S.len, rows, S.nslices, S.slice_w, s_sl.as<int64_t>());
+    SME_TRY(scan_exclusive_i64(s_sl.as<int64_t>(), S.slice_off, S.nslices, s));
+    SME_CUDA(cudaMemcpyAsync(&S.entries, S.slice_off + S.nslices, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SME_CUDA(cudaStreamSynchronize(s));
+    return SME_OK;
+}
+
+template <typename real>
+static sme_status build_shard_t(sme_op op, int64_t m, int64_t n, int64_t nnz, const int32_t *rp, const int32_t *col,
+                                const real *val, cudaStream_t s)
+{
+    ShardInfo &I = *op->shard;
+    const int32_t P = I.parts, p = I.part;
+    SME_CUDA(cudaMemsetAsync(op->d_status, 0, sizeof(int), s));
+    validate_csr<real><<<nblk(m + 1), 256, 0, s>>>(m, n, nnz, rp, col, val, op->d_status);
+    int st = 0;
+    SME_CUDA(cudaMemcpyAsync(&st, op->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SME_CUDA(cudaStreamSynchronize(s));
+    if (st & ST_BAD_CSR) {
+        set_error("invalid CSR structure");
+        return SME_ERR_INVALID_CSR;
+    }
+    if (st & ST_BAD_VALUE) {
+        set_error("non-finite matrix value");
+        return SME_ERR_NONFINITE;
+    }
+    // The whole matrix's transpose (the same stable sort by column as an unsplit operator).
+    const int64_t nz1 = std::max<int64_t>(nnz, 1);
+    AsyncScratch g_row_len(s), g_row_of(s), g_col_len(s), g_col_ptr(s), g_t_idx(s), g_t_val(s), g_k0(s), g_k1(s),
+        g_e0(s), g_e1(s), g_ord(s), g_inv(s), g_gpos(s);
+    SME_CUDA(g_row_len.alloc(m * sizeof(int32_t)));
+    SME_CUDA(g_row_of.alloc(nz1 * sizeof(int32_t)));
+    SME_CUDA(g_col_len.alloc(n * sizeof(int32_t)));
+    SME_CUDA(g_col_ptr.alloc((n + 1) * sizeof(int32_t)));
+    SME_CUDA(g_t_idx.alloc(nz1 * sizeof(int32_t)));
+    SME_CUDA(g_t_val.alloc(nz1 * sizeof(real)));
+    SME_CUDA(g_k0.alloc(nz1 * sizeof(uint32_t)));
+    SME_CUDA(g_k1.alloc(nz1 * sizeof(uint32_t)));
+    SME_CUDA(g_e0.alloc(nz1 * sizeof(int32_t)));
+    SME_CUDA(g_e1.alloc(nz1 * sizeof(int32_t)));
+    SME_CUDA(g_ord.alloc((m + n) * sizeof(int32_t)));
+    SME_CUDA(g_inv.alloc((m + n) * sizeof(int32_t)));
+    SME_CUDA(g_gpos.alloc((m + n) * sizeof(int32_t)));
+    int32_t *row_len = g_row_len.as<int32_t>(), *row_of = g_row_of.as<int32_t>(), *col_len = g_col_len.as<int32_t>(),
+            *col_ptr = g_col_ptr.as<int32_t>(), *t_idx = g_t_idx.as<int32_t>();
+    real *t_val = g_t_val.as<real>();
+    uint32_t *k0 = g_k0.as<uint32_t>(), *k1 = g_k1.as<uint32_t>();
+    int32_t *e0 = g_e0.as<int32_t>(), *e1 = g_e1.as<int32_t>();
+    row_lengths<<<nblk(m), 256, 0, s>>>(rp, m, row_len, row_of);
+    if (nnz > 0) iota_u32<<<nblk(nnz), 256, 0, s>>>(k0, col, e0, nnz);
+    bool alt = false;
+    SME_TRY(radix_sort_pairs(k0, e0, k1, e1, nnz, bit_length((uint64_t)(n - 1)), s, &alt));
+    const uint32_t *skeys = alt ? k1 : k0;
+    const int32_t *se = alt ? e1 : e0;
+    col_ptr_from_sorted<<<nblk(nnz + 1), 256, 0, s>>>(skeys, nnz, n, col_ptr);
+    lengths_from_ptr<<<nblk(n), 256, 0, s>>>(col_ptr, n, col_len);
+    if (nnz > 0) gather_transpose<real><<<nblk(nnz), 256, 0, s>>>(se, row_of, val, nnz, t_idx, t_val);
+    SME_CUDA(cudaGetLastError());
+
+    // Block-major orders of all rows and all columns, and every index's global table position.
+    int32_t *ord_r = g_ord.as<int32_t>(), *ord_c = ord_r + m;
+    int32_t *inv_r = g_inv.as<int32_t>(), *inv_c = inv_r + m;
+    int32_t *gpos_r = g_gpos.as<int32_t>(), *gpos_c = gpos_r + m;
+    SME_TRY(block_major_order(m, P, row_len, ord_r, inv_r, s));
+    SME_TRY(block_major_order(n, P, col_len, ord_c, inv_c, s));
+    global_positions<<<nblk(m), 256, 0, s>>>(m, P, I.rchunk, inv_r, gpos_r);
+    global_positions<<<nblk(n), 256, 0, s>>>(n, P, I.cchunk, inv_c, gpos_c);
+
+    // This part: its row block of A and its column block of A^T, indices renumbered to global table positions.
+    SME_TRY(make_sell_part<real>(op, op->fwd, I.r1 - I.r0, I.r0, ord_r, row_len, s));
+    SME_TRY(make_sell_part<real>(op, op->bwd, I.c1 - I.c0, I.c0, ord_c, col_len, s));
+    SME_TRY(fill<real>(op, op->fwd, rp, col, val, gpos_c, s));
+    SME_TRY(fill<real>(op, op->bwd, col_ptr, t_idx, t_val, gpos_r, s));
+    SME_CUDA(cudaStreamSynchronize(s));
+    (void)p;
+    return SME_OK;
+}
+
+sme_status build_shard(sme_op op, int64_t m, int64_t n, int64_t nnz, const int32_t *rp, const int32_t *col,
+                       const void *vals, cudaStream_t s)
+{
+    if (op->dtype == SME_F64) return build_shard_t<double>(op, m, n, nnz, rp, col, (const double *)vals, s);
+    return build_shard_t<float>(op, m, n, nnz, rp, col, (const float *)vals, s);
+}
+
 sme_status build_sparse(sme_op op, const int32_t *rp, const int32_t *col, const void *vals, cudaStream_t s,
                         const uint32_t *row_group, const uint32_t *col_group, int group_bits)
 {

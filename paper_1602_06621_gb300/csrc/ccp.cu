@@ -415,6 +415,7 @@ static bool ccp_op_ok(sme_op op, const char *who)
 extern "C" sme_status sme_op_norm2(sme_op op, const void *u_bar, const void *v_bar, int32_t iters, double *norm,
                                    void *stream)
 {
+    SME_TRY(no_shard(op, "sme_op_norm2"));
     if (!ccp_op_ok(op, "sme_op_norm2") || !norm || iters < 1) {
         if (op && norm && iters < 1) set_error("sme_op_norm2: iters must be >= 1");
         return SME_ERR_ARG;
@@ -439,6 +440,7 @@ extern "C" sme_status sme_ccp_lasso(sme_op op, const void *u_bar, const void *v_
                                     int64_t history_cap, void *stream)
 {
     NvtxRange range("sme ccp lasso");
+    SME_TRY(no_shard(op, "sme_ccp_lasso"));
     if (!ccp_op_ok(op, "sme_ccp_lasso")) return SME_ERR_ARG;
     if (!b || !x || !p || !res || !(p->lambda > 0.0) || p->max_iters < 0 || history_cap < 0 ||
         (history_cap > 0 && !history)) {

@@ -394,6 +394,35 @@ __global__ void draw_probe_words(uint64_t seed, uint32_t t, uint32_t sid, int64_
     }
 }
 
+// One part of a split matrix: load the part's start state (vectors of the part's own rows / columns, index
+// i - base) into sorted order and write the part's chunk of the tables of iteration t (`tab` points at the
+// chunk).  Probe counters use the whole matrix's index, so every part draws the probes an unsplit run draws.
+template <typename real, int KW>
+__global__ void shard_load(int64_t rows, int64_t base, const int32_t *perm, const real *x_in, const real *xb_in, real *x,
+                           real *xb, void *tab, uint32_t t, uint32_t sid, uint32_t k0, uint32_t k1)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const int32_t i = perm[r];
+    const real xi = x_in[i - base];
+    x[r] = xi;
+    xb[r] = xb_in[i - base];
+    uint32_t w0, w1;
+    probe_words2((uint32_t)i, t, sid, k0, k1, w0, w1);
+    TabEntry<real, KW>::store(tab, r, dexp(xi), w0, w1);
+}
+
+template <typename real>
+__global__ void shard_store(int64_t rows, int64_t base, const int32_t *perm, const real *x, const real *xb, real *x_out,
+                            real *xb_out)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const int32_t i = perm[r];
+    x_out[i - base] = x[r];
+    xb_out[i - base] = xb[r];
+}
+
 // ------------------------------------------------------------------ host side
 
 static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -573,6 +602,21 @@ static void launch_load(sme_op op, int side, int kw, const real *x_in, const rea
 struct Resolved {
     double alpha, beta, gamma, M;
 };
+
+static Resolved resolve(sme_op op, double alpha, double beta, double gamma, double M);
+
+// Defaults from the whole matrix's sizes (a part of a split matrix has its blocks' sizes in op->m, op->n).
+static Resolved resolve_whole(sme_op op, double alpha, double beta, double gamma, double M)
+{
+    const double m = op->shard ? (double)op->shard->gm : (double)op->m;
+    const double n = op->shard ? (double)op->shard->gn : (double)op->n;
+    Resolved r;
+    r.alpha = alpha > 0 ? alpha : std::pow(n / m, 0.25);
+    r.beta = beta > 0 ? beta : std::pow(m / n, 0.25);
+    r.gamma = gamma > 0 ? gamma : 0.1;
+    r.M = M > 0 ? M : std::log(1e4);
+    return r;
+}
 
 static Resolved resolve(sme_op op, double alpha, double beta, double gamma, double M)
 {
@@ -935,6 +979,62 @@ static sme_status autotune_t(sme_op op, int k, cudaStream_t s, int *spc_out, int
     return SME_OK;
 }
 
+// ------------------------------------------------------------------ one part of a split matrix
+
+template <typename real>
+static sme_status shard_begin_t(sme_op op, const sme_equil_params *p, const real *u, const real *v, const real *ub,
+                                const real *vb, void *row_table, void *col_table, cudaStream_t s)
+{
+    const int k = p->k, kw = (k + 31) / 32;
+    SME_TRY(ensure_equil_workspace(op, kw));
+    const ShardInfo &I = *op->shard;
+    const int64_t eb = entry_bytes(op->dbl, kw);
+    const uint32_t sid_s = (uint32_t)p->stream_base, sid_w = sid_s + 1u;
+    const uint32_t k0 = (uint32_t)p->seed, k1 = (uint32_t)(p->seed >> 32), t = (uint32_t)p->t_begin;
+    char *rt = (char *)row_table + I.part * I.rchunk * eb, *ct = (char *)col_table + I.part * I.cchunk * eb;
+    if (op->dbl || kw == 2) {
+        shard_load<real, 2><<<nblk(op->m), 256, 0, s>>>(op->m, I.r0, op->fwd.perm, u, ub, (real *)op->ws.u,
+                                                        (real *)op->ws.ub, rt, t, sid_w, k0, k1);
+        shard_load<real, 2><<<nblk(op->n), 256, 0, s>>>(op->n, I.c0, op->bwd.perm, v, vb, (real *)op->ws.v,
+                                                        (real *)op->ws.vb, ct, t, sid_s, k0, k1);
+    } else {
+        shard_load<real, 1><<<nblk(op->m), 256, 0, s>>>(op->m, I.r0, op->fwd.perm, u, ub, (real *)op->ws.u,
+                                                        (real *)op->ws.ub, rt, t, sid_w, k0, k1);
+        shard_load<real, 1><<<nblk(op->n), 256, 0, s>>>(op->n, I.c0, op->bwd.perm, v, vb, (real *)op->ws.v,
+                                                        (real *)op->ws.vb, ct, t, sid_s, k0, k1);
+    }
+    SME_CUDA(cudaGetLastError());
+    return SME_OK;
+}
+
+// Iteration t of the part: its rows against the whole column table, its columns against the whole row table
+// (both gathered from every part), writing the part's chunks of the next tables.
+template <typename real>
+static sme_status shard_step_t(sme_op op, const sme_equil_params *p, int t, const void *row_in, const void *col_in,
+                               void *row_out, void *col_out, cudaStream_t s)
+{
+    const int k = p->k, kw = (k + 31) / 32;
+    const ShardInfo &I = *op->shard;
+    const int64_t eb = entry_bytes(op->dbl, kw);
+    const Resolved R = resolve_whole(op, p->alpha, p->beta, p->gamma, p->M);
+    const Shape sh = shape_for(op, k);
+    StepArgs<real> a = base_args<real>(op, 0, R, p->seed, sh);
+    a.tab_in[0] = col_in;
+    a.tab_in[1] = row_in;
+    a.tab_out[0] = (char *)row_out + I.part * I.rchunk * eb;
+    a.tab_out[1] = (char *)col_out + I.part * I.cchunk * eb;
+    a.eta = (real)(2.0 / (R.gamma * ((double)t + (double)p->t0 + 1.0)));
+    a.avg_new = (real)(2.0 / ((double)t + 2.0));
+    a.avg_old = (real)((double)t / ((double)t + 2.0));
+    a.t_next = (uint32_t)(t + 1);
+    a.sid_out[0] = (uint32_t)p->stream_base + 1u;
+    a.sid_out[1] = (uint32_t)p->stream_base;
+    a.mode = 0;
+    launch_iteration<real>(a, k, sh.spc, grid_for(op, sh), s);
+    SME_CUDA(cudaGetLastError());
+    return SME_OK;
+}
+
 sme_status autotune_sparse(sme_op op, int k, cudaStream_t s, int *spc, int *cols_first, float *ms)
 {
     if (op->dbl) return autotune_t<double>(op, k, s, spc, cols_first, ms);
@@ -979,6 +1079,7 @@ extern "C" sme_status sme_equilibrate(sme_op op, const sme_equil_params *p, void
                                       void *v_bar, void *stream)
 {
     NvtxRange range("sme equilibrate");
+    SME_TRY(no_shard(op, "sme_equilibrate"));
     if (!op || !p || !u || !v || !u_bar || !v_bar || p->T < 0 || p->t_begin < 1 || p->t0 < 0) {
         set_error("sme_equilibrate: bad arguments");
         return SME_ERR_ARG;
@@ -1009,6 +1110,7 @@ extern "C" sme_status sme_equilibrate_targets(sme_op op, const sme_equil_params 
                                               const void *col_targets_sq, void *u, void *v, void *u_bar,
                                               void *v_bar, void *stream)
 {
+    SME_TRY(no_shard(op, "sme_equilibrate_targets"));
     if (!op || !p || !row_targets_sq || !col_targets_sq || !u || !v || !u_bar || !v_bar || p->T < 0 ||
         p->t_begin < 1 || p->t0 < 0 || op->dense || op->batch) {
         set_error("sme_equilibrate_targets: bad arguments (sparse single operators only)");
@@ -1032,6 +1134,7 @@ extern "C" sme_status sme_equilibrate_targets(sme_op op, const sme_equil_params 
 extern "C" sme_status sme_equilibrate_symmetric(sme_op op, const sme_equil_params *p, void *u, void *u_bar,
                                                 void *stream)
 {
+    SME_TRY(no_shard(op, "sme_equilibrate_symmetric"));
     if (!op || !p || !u || !u_bar || p->T < 0 || p->t_begin < 1 || p->t0 < 0 || op->dense || op->batch ||
         op->m != op->n) {
         set_error("sme_equilibrate_symmetric: bad arguments (square sparse single operators only)");
@@ -1055,6 +1158,7 @@ extern "C" sme_status sme_equilibrate_block(sme_op op, const sme_equil_params *p
                                             const int64_t *col_block_ptr, void *u, void *v, void *u_bar,
                                             void *v_bar, void *stream)
 {
+    SME_TRY(no_shard(op, "sme_equilibrate_block"));
     if (!op || !p || !row_block_ptr || !col_block_ptr || !u || !v || !u_bar || !v_bar || p->T < 0 ||
         p->t_begin < 1 || p->t0 < 0 || op->dense || op->batch || p_blocks < 1 || q_blocks < 1) {
         set_error("sme_equilibrate_block: bad arguments (sparse single operators only)");
@@ -1093,6 +1197,7 @@ extern "C" sme_status sme_op_autotune(sme_op op, int32_t k, int32_t *slices_per_
                                       float *ms_per_iteration, void *stream)
 {
     NvtxRange range("sme autotune");
+    SME_TRY(no_shard(op, "sme_op_autotune"));
     if (!op || op->dense) {
         set_error("sme_op_autotune: sparse operators only");
         return SME_ERR_ARG;
@@ -1114,6 +1219,7 @@ extern "C" sme_status sme_op_autotune(sme_op op, int32_t k, int32_t *slices_per_
 extern "C" sme_status sme_estimate(sme_op op, const void *u, const void *v, int32_t t, int32_t k, uint64_t seed,
                                    int32_t stream_base, void *z_u, void *z_v, void *stream)
 {
+    SME_TRY(no_shard(op, "sme_estimate"));
     if (!op || !u || !v || t < 0) {
         set_error("sme_estimate: bad arguments");
         return SME_ERR_ARG;
@@ -1127,4 +1233,72 @@ extern "C" sme_status sme_estimate(sme_op op, const void *u, const void *v, int3
                               (float *)z_v, (cudaStream_t)stream);
     }
     return estimate_sparse(op, u, v, t, k, seed, stream_base, z_u, z_v, (cudaStream_t)stream);
+}
+
+static sme_status shard_args(sme_op op, const sme_equil_params *p, const char *where)
+{
+    if (!op || !p || !op->shard || p->T < 0 || p->t_begin < 1 || p->t0 < 0) {
+        set_error("%s: bad arguments (a part of a split matrix is required)", where);
+        return SME_ERR_ARG;
+    }
+    if (!k_supported(p->k)) {
+        set_error("%s: k=%d not supported (1,2,4,...,64)", where, p->k);
+        return SME_ERR_UNSUPPORTED;
+    }
+    return SME_OK;
+}
+
+extern "C" sme_status sme_shard_begin(sme_op op, const sme_equil_params *p, const void *u, const void *v,
+                                      const void *u_bar, const void *v_bar, void *row_table, void *col_table,
+                                      void *stream)
+{
+    NvtxRange range("sme shard begin");
+    SME_TRY(shard_args(op, p, "sme_shard_begin"));
+    if (!u || !v || !u_bar || !v_bar || !row_table || !col_table) {
+        set_error("sme_shard_begin: null pointer");
+        return SME_ERR_ARG;
+    }
+    if (op->dbl)
+        return shard_begin_t<double>(op, p, (const double *)u, (const double *)v, (const double *)u_bar,
+                                     (const double *)v_bar, row_table, col_table, (cudaStream_t)stream);
+    return shard_begin_t<float>(op, p, (const float *)u, (const float *)v, (const float *)u_bar, (const float *)v_bar,
+                                row_table, col_table, (cudaStream_t)stream);
+}
+
+extern "C" sme_status sme_shard_step(sme_op op, const sme_equil_params *p, int32_t t, const void *row_table_in,
+                                     const void *col_table_in, void *row_table_out, void *col_table_out, void *stream)
+{
+    SME_TRY(shard_args(op, p, "sme_shard_step"));
+    if (t < 1 || !row_table_in || !col_table_in || !row_table_out || !col_table_out || row_table_in == row_table_out ||
+        col_table_in == col_table_out) {
+        set_error("sme_shard_step: bad iteration or tables (the next tables must be other buffers)");
+        return SME_ERR_ARG;
+    }
+    if (op->dbl)
+        return shard_step_t<double>(op, p, t, row_table_in, col_table_in, row_table_out, col_table_out,
+                                    (cudaStream_t)stream);
+    return shard_step_t<float>(op, p, t, row_table_in, col_table_in, row_table_out, col_table_out, (cudaStream_t)stream);
+}
+
+extern "C" sme_status sme_shard_end(sme_op op, void *u, void *v, void *u_bar, void *v_bar, void *stream)
+{
+    if (!op || !op->shard || !u || !v || !u_bar || !v_bar || !op->ws.u) {
+        set_error("sme_shard_end: bad arguments (call sme_shard_begin first)");
+        return SME_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const ShardInfo &I = *op->shard;
+    if (op->dbl) {
+        shard_store<double><<<nblk(op->m), 256, 0, s>>>(op->m, I.r0, op->fwd.perm, (double *)op->ws.u,
+                                                        (double *)op->ws.ub, (double *)u, (double *)u_bar);
+        shard_store<double><<<nblk(op->n), 256, 0, s>>>(op->n, I.c0, op->bwd.perm, (double *)op->ws.v,
+                                                        (double *)op->ws.vb, (double *)v, (double *)v_bar);
+    } else {
+        shard_store<float><<<nblk(op->m), 256, 0, s>>>(op->m, I.r0, op->fwd.perm, (float *)op->ws.u, (float *)op->ws.ub,
+                                                       (float *)u, (float *)u_bar);
+        shard_store<float><<<nblk(op->n), 256, 0, s>>>(op->n, I.c0, op->bwd.perm, (float *)op->ws.v, (float *)op->ws.vb,
+                                                       (float *)v, (float *)v_bar);
+    }
+    SME_CUDA(cudaGetLastError());
+    return SME_OK;
 }

@@ -740,6 +740,7 @@ extern "C" sme_status sme_evaluate(sme_op op, const void *u, const void *v, doub
                                    double *r2, double *c2, sme_eval_result *res, void *stream)
 {
     NvtxRange range("sme evaluate");
+    SME_TRY(no_shard(op, "sme_evaluate"));
     if (!op || !u || !v || !res) {
         set_error("sme_evaluate: bad arguments");
         return SME_ERR_ARG;
@@ -774,6 +775,7 @@ extern "C" sme_status sme_lsqr(sme_op op, const void *u_bar, const void *v_bar, 
                                const sme_lsqr_params *p, sme_lsqr_result *res, void *stream)
 {
     NvtxRange range("sme lsqr");
+    SME_TRY(no_shard(op, "sme_lsqr"));
     if (!op || !b || !x || !p || !res || p->max_iters < 0 || p->tol < 0 || (p->stop_rule != 0 && p->stop_rule != 1) ||
         p->history_cap < 0 || (p->history_cap > 0 && !p->history)) {
         set_error("sme_lsqr: bad arguments");

@@ -555,6 +555,7 @@ extern "C" sme_status sme_mlp_train_step(sme_mlp M, const float *X, const float 
 extern "C" sme_status sme_op_features(sme_op op, uint64_t seed, float *row_features, float *col_features,
                                       void *stream)
 {
+    SME_TRY(no_shard(op, "sme_op_features"));
     if (!op || op->dense) {
         set_error("sme_op_features: sparse operators only");
         return SME_ERR_ARG;
@@ -566,6 +567,7 @@ extern "C" sme_status sme_op_features(sme_op op, uint64_t seed, float *row_featu
 extern "C" sme_status sme_warm_start(sme_op op, sme_mlp M, uint64_t seed, void *u0, void *v0, void *stream)
 {
     NvtxRange range("sme warm start");
+    SME_TRY(no_shard(op, "sme_warm_start"));
     if (!op || !M || !u0 || !v0 || op->dense) {
         set_error("sme_warm_start: bad arguments");
         return SME_ERR_ARG;

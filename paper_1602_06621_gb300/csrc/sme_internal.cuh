@@ -176,6 +176,19 @@ struct GraphCache {
 
 struct DenseOp;  // tensor-core operator (dense A)
 
+// One part of a matrix split over several devices (shard.cu, build_kernels.cu): rows and columns are cut into
+// `parts` contiguous blocks, block q = [n q / parts, n (q + 1) / parts).  This part owns row block `part` of A
+// (its forward products) and column block `part` of A^T (its backward products).  The gather tables of the
+// whole matrix are laid out block-major in chunks of row_chunk (col_chunk) entries, chunk q at q * chunk, each
+// block's rows in descending-length order inside its chunk; the sliced-ELL copies of the part store these
+// global table positions.  The op's m, n are the part's block sizes.
+struct ShardInfo {
+    int32_t parts = 1, part = 0;
+    int64_t gm = 0, gn = 0, gnnz = 0;       // the whole matrix
+    int64_t r0 = 0, r1 = 0, c0 = 0, c1 = 0;  // this part's rows [r0, r1) and columns [c0, c1)
+    int64_t rchunk = 0, cchunk = 0;          // table entries per part (the largest block)
+};
+
 // A batch of matrices held as one block-diagonal operator (batch.cu).
 struct BatchInfo {
     int32_t count = 0;
@@ -200,6 +213,7 @@ struct sme_op_s {
     sme::GraphCache graph;
     sme::DenseOp *dense = nullptr;
     sme::BatchInfo *batch = nullptr;
+    sme::ShardInfo *shard = nullptr;
     int *d_status = nullptr;
     int64_t device_bytes = 0;
     struct {
@@ -233,10 +247,15 @@ sme_status radix_sort_pairs(uint32_t *keys, int32_t *vals, uint32_t *keys_alt, i
 sme_status build_sparse(sme_op op, const int32_t *d_row_ptr, const int32_t *d_col, const void *d_vals,
                         cudaStream_t s, const uint32_t *row_group = nullptr, const uint32_t *col_group = nullptr,
                         int group_bits = 0);
+// Builds the two sliced-ELL copies of one part of a split matrix (see ShardInfo) from the whole matrix's CSR
+// (m x n, nnz on the device); fills op->shard's blocks and chunks and sets op->m, op->n to the part's sizes.
+sme_status build_shard(sme_op op, int64_t m, int64_t n, int64_t nnz, const int32_t *d_row_ptr, const int32_t *d_col,
+                       const void *d_vals, cudaStream_t s);
 // sme_op_create_csr with optional host group ids (see build_sparse); used for batches.
 sme_status create_csr_grouped(sme_op *out, int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr,
                               const int32_t *col_idx, const void *vals, sme_dtype dtype, int on_device, void *stream,
-                              const uint32_t *row_group_host, const uint32_t *col_group_host, int group_bits);
+                              const uint32_t *row_group_host, const uint32_t *col_group_host, int group_bits,
+                              int32_t shard_parts = 0, int32_t shard_part = 0);
 
 // Equilibration / estimation launches (equilibrate.cu).
 sme_status ensure_equil_workspace(sme_op op, int kw);
@@ -263,6 +282,17 @@ sme_status dense_exact_norms(sme_op op, const float *u, const float *v, double *
                              double *c2, cudaStream_t s);
 sme_status dense_estimate(sme_op op, const float *u, const float *v, int t, int k, uint64_t seed, int sb,
                           float *zu, float *zv, cudaStream_t s);
+
+// Entry points that run the whole-matrix kernels refuse one part of a split matrix: its sliced-ELL indices are
+// positions in the whole matrix's tables, which only the sme_shard_* calls provide.
+inline sme_status no_shard(sme_op op, const char *where)
+{
+    if (op && op->shard) {
+        set_error("%s: the operator is one part of a split matrix (drive it with sme_shard_*)", where);
+        return SME_ERR_UNSUPPORTED;
+    }
+    return SME_OK;
+}
 
 inline int bit_length(uint64_t x)
 {

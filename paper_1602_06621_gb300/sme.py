@@ -18,7 +18,8 @@ __all__ = [
     "SmeError", "load", "SME_F64", "SME_F32", "SME_BF16", "SME_FP8E4M3", "SME_EQ_ASYNC", "SME_EQ_NO_GRAPH", "SME_EQ_TIMED",
     "sme_op_create_csr", "sme_op_create_dense", "sme_op_destroy", "sme_op_get_info", "sme_draw_probes",
     "sme_equilibrate", "sme_op_check", "sme_estimate", "sme_evaluate", "sme_lsqr", "sme_status_string",
-    "sme_estimate_rows_static", "SME_STATIC_MAX_COLS", "sme_batch_create", "sme_batch_destroy",
+    "sme_estimate_rows_static", "SME_STATIC_MAX_COLS", "sme_op_create_csr_shard", "sme_shard_get_info",
+    "sme_shard_begin", "sme_shard_step", "sme_shard_end", "sme_batch_create", "sme_batch_destroy",
     "sme_batch_get_info", "sme_batch_equilibrate", "sme_batch_estimate", "sme_batch_op", "sme_op_autotune", "sme_batch_lsqr",
     "sme_equilibrate_targets", "sme_equilibrate_symmetric", "sme_equilibrate_block", "sme_mlp_create",
     "sme_mlp_destroy", "sme_mlp_param_count", "sme_mlp_get_params", "sme_mlp_set_params", "sme_mlp_forward",
@@ -70,6 +71,13 @@ class sme_ccp_result(ctypes.Structure):
                 ("rel_gap", ctypes.c_double), ("op_norm", ctypes.c_double), ("tau", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("converged", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
                 ("history_count", ctypes.c_int64)]
+
+
+class sme_shard_info(ctypes.Structure):
+    _fields_ = [("parts", ctypes.c_int32), ("part", ctypes.c_int32), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64), ("col_begin", ctypes.c_int64),
+                ("col_end", ctypes.c_int64), ("row_chunk", ctypes.c_int64), ("col_chunk", ctypes.c_int64),
+                ("entry_bytes", ctypes.c_int32)]
 
 
 class sme_lsqr_params(ctypes.Structure):
@@ -131,6 +139,12 @@ SIGNATURES = {
     "sme_batch_warm_start": ([_vp, _vp, _u64, _vp, _vp, _vp], _i32),
     "sme_op_norm2": ([_vp, _vp, _vp, _i32, ctypes.POINTER(ctypes.c_double), _vp], _i32),
     "sme_ccp_lasso": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp], _i32),
+    "sme_op_create_csr_shard": ([ctypes.POINTER(_vp), _i64, _i64, _i64, _vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp],
+                                _i32),
+    "sme_shard_get_info": ([_vp, _i32, ctypes.POINTER(sme_shard_info)], _i32),
+    "sme_shard_begin": ([_vp, ctypes.POINTER(sme_equil_params), _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
+    "sme_shard_step": ([_vp, ctypes.POINTER(sme_equil_params), _i32, _vp, _vp, _vp, _vp, _vp], _i32),
+    "sme_shard_end": ([_vp, _vp, _vp, _vp, _vp, _vp], _i32),
 }
 
 
@@ -202,6 +216,57 @@ def sme_op_create_csr(m, n, row_ptr, col_idx, vals, dtype=None, stream=None):
                                   int(dtype), int(on_device), _stream(stream))
     _check(st, "sme_op_create_csr")
     return op
+
+
+def sme_op_create_csr_shard(m, n, row_ptr, col_idx, vals, parts, part, dtype=None, stream=None):
+    """Create part `part` of `parts` of a sparse matrix split over several devices (arguments as
+    sme_op_create_csr, the whole matrix is passed)."""
+    on_device = not isinstance(row_ptr, np.ndarray)
+    if on_device:
+        import torch
+        if dtype is None:
+            dtype = SME_F64 if vals.dtype == torch.float64 else SME_F32
+        nnz = int(col_idx.numel())
+    else:
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+        if dtype is None:
+            dtype = SME_F64 if vals.dtype == np.float64 else SME_F32
+        vals = np.ascontiguousarray(vals, dtype=np.float64 if dtype == SME_F64 else np.float32)
+        nnz = int(col_idx.size)
+    op = ctypes.c_void_p()
+    st = load().sme_op_create_csr_shard(ctypes.byref(op), int(m), int(n), nnz, _ptr(row_ptr), _ptr(col_idx),
+                                        _ptr(vals), int(dtype), int(on_device), int(parts), int(part), _stream(stream))
+    _check(st, "sme_op_create_csr_shard")
+    return op
+
+
+def sme_shard_get_info(op, k) -> dict:
+    """Blocks, table chunks and table entry size of a part of a split matrix."""
+    info = sme_shard_info()
+    _check(load().sme_shard_get_info(op, int(k), ctypes.byref(info)), "sme_shard_get_info")
+    return {f: getattr(info, f) for f, _ in sme_shard_info._fields_}
+
+
+def sme_shard_begin(op, u, v, u_bar, v_bar, row_table, col_table, *, T, k, t_begin=1, t0=0, seed=0, stream_base=0,
+                    alpha=0.0, beta=0.0, gamma=0.0, M=0.0, stream=None):
+    """Load this part's start state and write its chunks of the tables of iteration t_begin."""
+    p = sme_equil_params(alpha, beta, gamma, M, int(T), int(k), int(t_begin), int(t0), int(seed), int(stream_base), 0)
+    _check(load().sme_shard_begin(op, ctypes.byref(p), _ptr(u), _ptr(v), _ptr(u_bar), _ptr(v_bar), _ptr(row_table),
+                                  _ptr(col_table), _stream(stream)), "sme_shard_begin")
+
+
+def sme_shard_step(op, t, row_in, col_in, row_out, col_out, *, T, k, t_begin=1, t0=0, seed=0, stream_base=0,
+                   alpha=0.0, beta=0.0, gamma=0.0, M=0.0, stream=None):
+    """Iteration t of this part: whole current tables in, this part's chunks of the next tables out."""
+    p = sme_equil_params(alpha, beta, gamma, M, int(T), int(k), int(t_begin), int(t0), int(seed), int(stream_base), 0)
+    _check(load().sme_shard_step(op, ctypes.byref(p), int(t), _ptr(row_in), _ptr(col_in), _ptr(row_out), _ptr(col_out),
+                                 _stream(stream)), "sme_shard_step")
+
+
+def sme_shard_end(op, u, v, u_bar, v_bar, stream=None):
+    """This part's u, v, u_bar, v_bar after the last step."""
+    _check(load().sme_shard_end(op, _ptr(u), _ptr(v), _ptr(u_bar), _ptr(v_bar), _stream(stream)), "sme_shard_end")
 
 
 def sme_op_create_dense(m, n, A, lda=None, dtype=SME_BF16, row_scales=None, stream=None):
