@@ -113,7 +113,8 @@ def parse():
                     help="dense workload: which storages to run (bf16, fp8 or both, comma-separated)")
     ap.add_argument("--plain-cap", type=int, default=20000,
                     help="iteration cap of the plain-LSQR comparison (min(200 n, 1e6) is the long reading)")
-    ap.add_argument("--workload", choices=["large", "dense", "batched", "learned", "ccp", "lsqr"], default="large",
+    ap.add_argument("--workload", choices=["large", "dense", "batched", "learned", "ccp", "lsqr", "sharded"],
+                    default="large",
                     help="large: the sparse 1e6 x 5e5 step (default); dense: 16384^2 BF16 tensor-core step; "
                          "batched: 512 matrices of uneven size in one operator; learned: warm start vs zero "
                          "start to a norm spread of 1.05 on 500 held-out matrices; ccp: the Lasso of Section 5.2 "
@@ -501,6 +502,66 @@ def dense_line(args, rank, world, local):
     if op8 is not None:
         sme.sme_op_destroy(op8)
     return line
+
+
+# ------------------------------------------------------------------------------------------ one matrix, split
+
+def run_sharded(args, rank, world, local):
+    """T iterations of Algorithm 1 (k = 32) on ONE large matrix (1e6 x 5e5, seed 2) split over the job's GPUs:
+    rank r holds row block r of A and column block r of A^T, and the two gather tables are all-gathered
+    (NCCL, in place) after every iteration.  Strong scaling: the work is fixed as N grows.  With one GPU
+    the exchange has nothing to do and the part is the whole matrix."""
+    import torch
+
+    from paper_1602_06621_gb300 import inputs as I
+    from paper_1602_06621_gb300 import shard as SH
+    from paper_1602_06621_gb300 import sme
+
+    torch.cuda.set_device(local)
+    ranks = Ranks(rank, world, local)
+    k, T = args.k, args.T
+    A = I.workload_large(args.scale, seed=2)
+    op = sme.sme_op_create_csr_shard(A.m, A.n, A.row_ptr, A.col_idx, A.vals, world, rank)
+    part = SH.Part(op, k, f"cuda:{local}")
+    exchange = SH.CollectiveExchange() if world > 1 else SH.LocalExchange()
+
+    def step():
+        for x in (part.u, part.v, part.u_bar, part.v_bar):
+            x.zero_()
+        SH.run([part], exchange, T=T, k=k, seed=0)
+
+    for _ in range(args.warmup):
+        step()
+    sme.sme_op_check(op)
+    ranks.barrier()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            step()
+        ev1.record()
+        torch.cuda.synchronize()
+        ranks.barrier()
+    sme.sme_op_check(op)
+    elapsed = ranks.max(ev0.elapsed_time(ev1) / 1e3)
+    info = part.info
+    table_bytes = (A.m + A.n) * info["entry_bytes"]
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": k * T * args.steps / elapsed, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(A, k, T) + f"; split over {world} GPU(s) (row blocks of A, column "
+                                                            f"blocks of A^T), tables all-gathered every iteration",
+                       "m": A.m, "n": A.n, "nnz": A.nnz, "k": k, "T": T, "parallelism": f"split x{world}",
+                       "exchange_bytes_per_iteration": table_bytes},
+            "gpu_launches": (T + 2) * args.steps, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    sme.sme_op_destroy(op)
+    ranks.close()
+    return 0
 
 
 # ------------------------------------------------------------------------------------------ batched workload
@@ -971,6 +1032,8 @@ def main():
         return run_ccp(args, rank, world, local)
     if args.workload == "lsqr":
         return run_lsqr_paper(args, rank, world, local)
+    if args.workload == "sharded":
+        return run_sharded(args, rank, world, local)
 
     import numpy as np
 
