@@ -159,6 +159,11 @@ typedef struct {
 #define SME_EQ_ASYNC 1    /* do not synchronise or read the status word; see sme_op_check */
 #define SME_EQ_NO_GRAPH 2 /* launch the iterations directly instead of through a cached CUDA graph */
 #define SME_EQ_TIMED 4    /* time the iteration loop with CUDA events on `stream` (read by sme_op_get_info) */
+/* Test of the failure path of the tensor-core (dense) operators: the TMA producer's and the MMA issuer's
+ * waits get a bound of zero polls, so every launch gives up before its first MMA, writes no iterate, and the
+ * call returns SME_ERR_TIMEOUT; the drain waits (the accumulator, MMAs in flight before TMEM is freed, copies
+ * landing) keep their full bound.  The iterates are left as passed in.  Sparse operators ignore it. */
+#define SME_EQ_EXPIRE_PIPELINE_WAITS 8
 
 /*
  * sme_equilibrate -- iterations t_begin .. t_begin+T-1 of Algorithm 1 (Section 3.2):

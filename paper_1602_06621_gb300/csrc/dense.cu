@@ -88,6 +88,8 @@ struct DenseArgs {
     uint32_t t_next, key0, key1, sid_out[2];
     int mode;                 // 0 step, 1 estimate only
     const float *row_scale;   // A_ij = row_scale[i] * Abf16_ij (FP8 input), or null
+    uint32_t pipe_limit;      // TC_WAIT_LIMIT, or 0 to launch the EXPIRE instantiation (test of the timeout
+                              // path); the drain waits always use TC_WAIT_LIMIT
     int *status;
 };
 
@@ -96,9 +98,12 @@ struct DenseMaps {
     CUtensorMap B[2];  // [0] forward operand (current), [1] backward operand (current)
 };
 
-template <int KP>
+// EXPIRE: the instantiation for the test of the timeout path (producer and MMA-issuer waits bounded by zero
+// polls); the bound is a compile-time constant so that the normal kernel's issuing loops stay minimal.
+template <int KP, bool EXPIRE = false>
 __global__ void __launch_bounds__(DN_THREADS, 1) dense_iteration(const __grid_constant__ DenseMaps maps, DenseArgs a)
 {
+    constexpr uint32_t PIPE_LIMIT = EXPIRE ? 0u : TC_WAIT_LIMIT;
     using C = DenseCfg<KP>;
     constexpr int NT = C::NT;  // accumulator columns: hi then lo
     constexpr int UNITS = C::UNITS, NA = C::A_SLOTS, NB = C::B_SLOTS;
@@ -159,7 +164,7 @@ __global__ void __launch_bounds__(DN_THREADS, 1) dense_iteration(const __grid_co
         bool bad = false;
         for (int kb = 0; kb < nk && !bad; ++kb) {
             const int sa = kb % NA;
-            if (kb >= NA && !mbar_wait(&a_empty[sa], ((kb / NA) - 1) & 1)) {
+            if (kb >= NA && !mbar_wait_n(&a_empty[sa], ((kb / NA) - 1) & 1, PIPE_LIMIT)) {
                 bad = true;
                 break;
             }
@@ -167,7 +172,7 @@ __global__ void __launch_bounds__(DN_THREADS, 1) dense_iteration(const __grid_co
             tma_load_2d_pair(ring_a + sa * DN_A_SLOT, mapX, 0, (tile * nk + kb) * DN_BM, cluster_addr(&a_full[sa], 0));
             for (int j = 0; j < UNITS; ++j) {
                 const int q = kb * UNITS + j, sb = q % NB;
-                if (q >= NB && !mbar_wait(&b_empty[sb], ((q / NB) - 1) & 1)) {
+                if (q >= NB && !mbar_wait_n(&b_empty[sb], ((q / NB) - 1) & 1, PIPE_LIMIT)) {
                     bad = true;
                     break;
                 }
@@ -185,14 +190,14 @@ __global__ void __launch_bounds__(DN_THREADS, 1) dense_iteration(const __grid_co
         bool bad = false;
         for (int kb = 0; kb < nk && !bad; ++kb) {
             const int sa = kb % NA;
-            if (!mbar_wait(&a_full[sa], (kb / NA) & 1)) {
+            if (!mbar_wait_n(&a_full[sa], (kb / NA) & 1, PIPE_LIMIT)) {
                 bad = true;
                 break;
             }
             const uint64_t ad0 = smem_desc_sw128_u32(sbase + (uint32_t)(sa * DN_A_SLOT));
             for (int j = 0; j < UNITS; ++j) {
                 const int q = kb * UNITS + j, sb = q % NB;
-                if (!mbar_wait(&b_full[sb], (q / NB) & 1)) {
+                if (!mbar_wait_n(&b_full[sb], (q / NB) & 1, PIPE_LIMIT)) {
                     bad = true;
                     break;
                 }
@@ -389,13 +394,14 @@ static sme_status ensure_dense_workspace(sme_op op, int kp)
     return SME_OK;
 }
 
-template <int KP>
+template <int KP, bool EXPIRE>
 static sme_status launch_dense(const DenseMaps &maps, const DenseArgs &a, int grid, cudaStream_t s)
 {
     const size_t smem = dense_smem<KP>();
     static bool attr_set = false;
     if (!attr_set) {
-        SME_CUDA(cudaFuncSetAttribute(dense_iteration<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SME_CUDA(cudaFuncSetAttribute(dense_iteration<KP, EXPIRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
         attr_set = true;
     }
     cudaLaunchConfig_t cfg = {};
@@ -410,7 +416,7 @@ static sme_status launch_dense(const DenseMaps &maps, const DenseArgs &a, int gr
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    SME_CUDA(cudaLaunchKernelEx(&cfg, dense_iteration<KP>, maps, a));
+    SME_CUDA(cudaLaunchKernelEx(&cfg, dense_iteration<KP, EXPIRE>, maps, a));
     return SME_OK;
 }
 
@@ -423,8 +429,12 @@ static sme_status run_dense(sme_op op, const DenseArgs &a, int buf, cudaStream_t
     maps.B[0] = D->mapBf[buf];
     maps.B[1] = D->mapBb[buf];
     const int grid = a.row_ctas + ((a.col_tiles + 1) & ~1);  // whole clusters of two on each product
-    if (a.kp == 256) return launch_dense<256>(maps, a, grid, s);
-    return launch_dense<128>(maps, a, grid, s);
+    if (a.pipe_limit == 0) {
+        if (a.kp == 256) return launch_dense<256, true>(maps, a, grid, s);
+        return launch_dense<128, true>(maps, a, grid, s);
+    }
+    if (a.kp == 256) return launch_dense<256, false>(maps, a, grid, s);
+    return launch_dense<128, false>(maps, a, grid, s);
 }
 
 static DenseArgs dense_base(sme_op op, double alpha, double beta, double gamma, double M, uint64_t seed, int kp)
@@ -448,6 +458,7 @@ static DenseArgs dense_base(sme_op op, double alpha, double beta, double gamma, 
     a.key0 = (uint32_t)seed;
     a.key1 = (uint32_t)(seed >> 32);
     a.row_scale = D->row_scale;
+    a.pipe_limit = TC_WAIT_LIMIT;
     a.status = op->d_status;
     return a;
 }
@@ -526,6 +537,7 @@ sme_status dense_equilibrate(sme_op op, const sme_equil_params *p, float *u, flo
         a.sid_out[0] = sid_w;
         a.sid_out[1] = sid_s;
         a.mode = 0;
+        if (p->flags & SME_EQ_EXPIRE_PIPELINE_WAITS) a.pipe_limit = 0;
         SME_TRY(run_dense(op, a, cur, s));
     }
     if (timed) {

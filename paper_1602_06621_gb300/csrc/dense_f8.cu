@@ -145,6 +145,7 @@ struct DenseArgs8 {
     const uint32_t *q_prev;    // [side] keys of max (x^{t-1} + log|c|)
     uint32_t *q_cur;           // [side] keys of max (x^t + log|c|), filled here
     uint32_t *q_clear;         // [side] the ring slot the next launch fills, cleared here
+    uint32_t pipe_limit;       // TC_WAIT_LIMIT, or 0 to launch the EXPIRE instantiation (see dense.cu)
     int *status;
 };
 
@@ -157,9 +158,11 @@ __device__ __forceinline__ float f8_next_bound(const DenseArgs8 &a, int side)
     return fminf(U, a.M + a.logc[side]);
 }
 
-template <int KP>
+// EXPIRE: the instantiation for the test of the timeout path (see dense.cu).
+template <int KP, bool EXPIRE = false>
 __global__ void __launch_bounds__(F8_THREADS, 1) dense_iteration_f8(const __grid_constant__ DenseMaps8 maps, DenseArgs8 a)
 {
+    constexpr uint32_t PIPE_LIMIT = EXPIRE ? 0u : TC_WAIT_LIMIT;
     using C = F8Cfg<KP>;
     constexpr int NS = C::STAGES;
     constexpr uint32_t IDESC = idesc_e4m3(2 * F8_BM, KP);
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(F8_THREADS, 1) dense_iteration_f8(const __grid
         bool bad = false;
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb % NS;
-            if (kb >= NS && !mbar_wait(&empty[s], ((kb / NS) - 1) & 1)) {
+            if (kb >= NS && !mbar_wait_n(&empty[s], ((kb / NS) - 1) & 1, PIPE_LIMIT)) {
                 bad = true;
                 break;
             }
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(F8_THREADS, 1) dense_iteration_f8(const __grid
         bool bad = false;
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb % NS;
-            if (!mbar_wait(&full[s], (kb / NS) & 1)) {
+            if (!mbar_wait_n(&full[s], (kb / NS) & 1, PIPE_LIMIT)) {
                 bad = true;
                 break;
             }
@@ -432,13 +435,14 @@ __global__ void f8_row_norms(const uint8_t *X, int64_t rows, int64_t cols, const
 
 static inline unsigned nblk8(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-template <int KP>
+template <int KP, bool EXPIRE>
 static sme_status launch_f8(const DenseMaps8 &maps, const DenseArgs8 &a, int grid, cudaStream_t s)
 {
     const size_t smem = (size_t)F8Cfg<KP>::BYTES + 1024;
     static bool attr_set = false;
     if (!attr_set) {
-        SME_CUDA(cudaFuncSetAttribute(dense_iteration_f8<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SME_CUDA(cudaFuncSetAttribute(dense_iteration_f8<KP, EXPIRE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
         attr_set = true;
     }
     cudaLaunchConfig_t cfg = {};
@@ -453,7 +457,7 @@ static sme_status launch_f8(const DenseMaps8 &maps, const DenseArgs8 &a, int gri
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    SME_CUDA(cudaLaunchKernelEx(&cfg, dense_iteration_f8<KP>, maps, a));
+    SME_CUDA(cudaLaunchKernelEx(&cfg, dense_iteration_f8<KP, EXPIRE>, maps, a));
     return SME_OK;
 }
 
@@ -522,8 +526,12 @@ static sme_status run_f8(sme_op op, const DenseArgs8 &a, int buf, cudaStream_t s
     maps.B[0] = D->mapBf8[buf];
     maps.B[1] = D->mapBb8[buf];
     const int grid = a.row_ctas + ((a.col_tiles + 1) & ~1);
-    if (a.kp == 256) return launch_f8<256>(maps, a, grid, s);
-    return launch_f8<128>(maps, a, grid, s);
+    if (a.pipe_limit == 0) {
+        if (a.kp == 256) return launch_f8<256, true>(maps, a, grid, s);
+        return launch_f8<128, true>(maps, a, grid, s);
+    }
+    if (a.kp == 256) return launch_f8<256, false>(maps, a, grid, s);
+    return launch_f8<128, false>(maps, a, grid, s);
 }
 
 static DenseArgs8 f8_base(sme_op op, double alpha, double beta, double gamma, double M, uint64_t seed, int kp)
@@ -549,6 +557,7 @@ static DenseArgs8 f8_base(sme_op op, double alpha, double beta, double gamma, do
     a.row_scale = D->row_scale;
     a.logc[0] = D->logc_max;
     a.logc[1] = 0.f;
+    a.pipe_limit = TC_WAIT_LIMIT;
     a.status = op->d_status;
     return a;
 }
@@ -611,6 +620,7 @@ sme_status dense_f8_equilibrate(sme_op op, const sme_equil_params *p, double alp
         a.q_prev = q + ((t - 1) % 3) * 2;
         a.q_cur = q + (t % 3) * 2;
         a.q_clear = q + ((t + 1) % 3) * 2;
+        if (p->flags & SME_EQ_EXPIRE_PIPELINE_WAITS) a.pipe_limit = 0;
         SME_TRY(run_f8(op, a, cur, s));
     }
     if (timed) {

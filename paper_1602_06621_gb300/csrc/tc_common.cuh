@@ -71,6 +71,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
+// Wait for phase `parity` of `bar` for at most `limit` polls; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait_n(uint64_t *bar, uint32_t parity, uint32_t limit)
+{
+    for (uint32_t i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
 // Bounded wait for phase `parity` of `bar`; false if it did not complete within the limit.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 {

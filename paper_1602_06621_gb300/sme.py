@@ -16,6 +16,7 @@ from .build import LIB, build_library
 
 __all__ = [
     "SmeError", "load", "SME_F64", "SME_F32", "SME_BF16", "SME_FP8E4M3", "SME_EQ_ASYNC", "SME_EQ_NO_GRAPH", "SME_EQ_TIMED",
+    "SME_EQ_EXPIRE_PIPELINE_WAITS",
     "sme_op_create_csr", "sme_op_create_dense", "sme_op_destroy", "sme_op_get_info", "sme_draw_probes",
     "sme_equilibrate", "sme_op_check", "sme_estimate", "sme_evaluate", "sme_lsqr", "sme_status_string",
     "sme_estimate_rows_static", "SME_STATIC_MAX_COLS", "sme_op_create_csr_shard", "sme_shard_get_info",
@@ -29,7 +30,7 @@ __all__ = [
 SME_STATIC_MAX_COLS = 1 << 20
 
 SME_F64, SME_F32, SME_BF16, SME_FP8E4M3 = 0, 1, 2, 3
-SME_EQ_ASYNC, SME_EQ_NO_GRAPH, SME_EQ_TIMED = 1, 2, 4
+SME_EQ_ASYNC, SME_EQ_NO_GRAPH, SME_EQ_TIMED, SME_EQ_EXPIRE_PIPELINE_WAITS = 1, 2, 4, 8
 _STATUS = {0: "SME_OK", -1: "SME_ERR_ARG", -2: "SME_ERR_INVALID_CSR", -3: "SME_ERR_OOM", -4: "SME_ERR_CUDA",
            -5: "SME_ERR_NONFINITE", -6: "SME_ERR_TIMEOUT", -7: "SME_ERR_NOT_CONVERGED", -8: "SME_ERR_UNSUPPORTED"}
 

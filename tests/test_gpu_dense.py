@@ -358,6 +358,53 @@ def test_dense_fp8_full_size_sampled_estimate():
     assert np.all(np.abs(zv[cols] - ezv) <= _F8_ROUNDING_BOUND * c2)
 
 
+@pytest.mark.parametrize("fp8", [False, True])
+def test_dense_pipeline_waits_expire_without_writing(fp8):
+    """The failure path of the tensor-core kernels, without a GPU fault: with SME_EQ_EXPIRE_PIPELINE_WAITS the
+    producer's and the MMA issuer's waits give up at once, so every launch stops before its first MMA.  The
+    call must return SME_ERR_TIMEOUT and leave u, v and the averages exactly as passed in; the drain (the
+    accumulator barrier, TMEM released only once no MMA is in flight, copies in flight allowed to land) must
+    leave the operator usable: the next call on it, and a call on a fresh operator, equal an undisturbed
+    run bit for bit.  256 x 256, k = 256."""
+    import torch
+    m = n = 256
+    if fp8:
+        codes, scales, _ = _e4m3_matrix(m, n, seed=31)
+        make = lambda: _fp8_op(codes, scales)
+    else:
+        Ad, _ = _bf16_matrix(m, n, seed=31)
+        make = lambda: sme.sme_op_create_dense(m, n, Ad, dtype=sme.SME_BF16)
+
+    def run(op, start, flags=0):
+        g = [torch.tensor(x, dtype=torch.float32, device="cuda") for x in start]
+        sme.sme_equilibrate(op, *g, T=3, k=256, seed=4, flags=flags)
+        return [x.cpu().numpy() for x in g]
+
+    zero = [np.zeros(m, np.float32), np.zeros(n, np.float32), np.zeros(m, np.float32), np.zeros(n, np.float32)]
+    rng = np.random.default_rng(2)
+    start = [rng.normal(0, 0.3, x.size).astype(np.float32) for x in zero]
+    op = make()
+    try:
+        ref = run(op, zero)
+        g = [torch.tensor(x, device="cuda") for x in start]
+        with pytest.raises(sme.SmeError) as ei:
+            sme.sme_equilibrate(op, *g, T=3, k=256, seed=4, flags=sme.SME_EQ_EXPIRE_PIPELINE_WAITS)
+        assert ei.value.name == "SME_ERR_TIMEOUT"
+        for x, y in zip(g, start):
+            np.testing.assert_array_equal(x.cpu().numpy(), y)
+        again = run(op, zero)
+    finally:
+        sme.sme_op_destroy(op)
+    op = make()
+    try:
+        fresh = run(op, zero)
+    finally:
+        sme.sme_op_destroy(op)
+    for a, b, c in zip(ref, again, fresh):
+        np.testing.assert_array_equal(a, b)
+        np.testing.assert_array_equal(a, c)
+
+
 def test_dense_argument_errors():
     import torch
     A = torch.zeros((200, 256), dtype=torch.bfloat16, device="cuda")

@@ -163,6 +163,25 @@ def test_equilibrate_fp32_matches_oracle(scale, T):
     assert rel_norm(got[2:], ref[2:]) <= 1e-4
 
 
+def test_equilibrate_fp32_whole_run_at_a_tenth_of_the_large_workload():
+    """1e5 x 5e4 (a tenth of the large workload: 20 nonzeros per row, factors of variance 2), k = 32, T = 500:
+    the FP32 run against the FP64 oracle's whole run, norm-wise relative error of [u; v; ubar; vbar] and of
+    [ubar; vbar] <= 1e-4.  The oracle runs in its OpenMP build (the checker's bits, every host core)."""
+    A = I.workload_large(scale=0.1, seed=4)
+    op, dt = make_op(A)
+    try:
+        got = gpu_equilibrate(op, dt, A.m, A.n, T=500, k=32, seed=0)
+    finally:
+        sme.sme_op_destroy(op)
+    O.set_parallel(True)
+    try:
+        ref = O.equilibrate(O.OracleCSR.from_any(A), T=500, k=32, seed=0)
+    finally:
+        O.set_parallel(False)
+    assert rel_norm(got, ref) <= 1e-4, rel_norm(got, ref)
+    assert rel_norm(got[2:], ref[2:]) <= 1e-4
+
+
 def test_equilibrate_fp32_every_step_matches_oracle():
     A = I.workload_large(scale=0.004, seed=4)
     op, dt = make_op(A)
