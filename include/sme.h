@@ -431,6 +431,16 @@ sme_status sme_mlp_gradient(sme_mlp mlp, const float *X, const float *target, in
 /* One Adam step (beta1 0.9, beta2 0.999) on the same loss with learning rate lr. */
 sme_status sme_mlp_train_step(sme_mlp mlp, const float *X, const float *target, int64_t N, float lr, float *loss,
                               void *stream);
+/* Input normalisation fitted to training features X (N x 8 device floats, 16-byte aligned, N >= 2): the
+ * per-feature mean and standard deviation (N - 1 in the denominator; a deviation <= 1e-6 is replaced by 1),
+ * each summed in FP64 in a fixed order; then set as by sme_mlp_set_params.  Synchronises `stream`. */
+sme_status sme_mlp_fit_normalisation(sme_mlp mlp, const float *X, int64_t N, void *stream);
+/* A minibatch for sme_mlp_train_step: X_batch (batch x 8), target_batch (batch) filled with rows of (X, target)
+ * (N rows, N < 2^32) drawn uniformly with replacement.  Draw b of step `step` takes row floor(r N / 2^32), r the
+ * first output word of Philox4x32-10 at counter (b mod 2^32, b >> 32, step, 0x6D6C7000) with key
+ * (seed mod 2^32, seed >> 32).  X and X_batch 16-byte aligned. */
+sme_status sme_mlp_draw_batch(const float *X, const float *target, int64_t N, int64_t batch, uint64_t seed,
+                              int64_t step, float *X_batch, float *target_batch, void *stream);
 /* Features of every row (m x 8) and column (n x 8) of a sparse operator, device float arrays.  For the
  * operator of a batch, the mean sketch norms and the sizes are those of each row's / column's own matrix. */
 sme_status sme_op_features(sme_op op, uint64_t seed, float *row_features, float *col_features, void *stream);

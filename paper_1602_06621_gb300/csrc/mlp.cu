@@ -359,6 +359,65 @@ static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t -
 static size_t infer_smem() { return sizeof(MlpSmem); }
 static size_t grad_smem() { return sizeof(MlpSmem) + (size_t)MLP_H * W2P * sizeof(float); }
 
+// ------------------------------------------------------------------ training data on the device
+
+constexpr int NORM_THREADS = 256;
+constexpr int NORM_BLOCKS = 152 * 2;
+
+// Per-block FP64 sums over rows of X (N x 8) of x_f - shift_f (pass 1: shift = 0) or of (x_f - shift_f)^2
+// (pass 2: shift = the mean); rows split evenly over the blocks, each block sums its rows in order.
+__global__ void __launch_bounds__(NORM_THREADS) feature_sums(const float *X, int64_t N, const double *shift,
+                                                              int squared, double *partials)
+{
+    __shared__ double sh[NORM_THREADS][MLP_IN + 1];
+    double acc[MLP_IN];
+#pragma unroll
+    for (int f = 0; f < MLP_IN; ++f) acc[f] = 0.0;
+    const int64_t per = (N + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * per, hi = min(N, lo + per);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += NORM_THREADS)
+#pragma unroll
+        for (int f = 0; f < MLP_IN; ++f) {
+            const double d = (double)X[i * MLP_IN + f] - (shift ? shift[f] : 0.0);
+            acc[f] += squared ? d * d : d;
+        }
+#pragma unroll
+    for (int f = 0; f < MLP_IN; ++f) sh[threadIdx.x][f] = acc[f];
+    __syncthreads();
+    if (threadIdx.x < MLP_IN) {
+        double t = 0.0;
+        for (int j = 0; j < NORM_THREADS; ++j) t += sh[j][threadIdx.x];
+        partials[(int64_t)blockIdx.x * MLP_IN + threadIdx.x] = t;
+    }
+}
+
+// out_f = (sum of the blocks' partials in block order) / div.
+__global__ void feature_finish(const double *partials, int nblocks, double div, double *out)
+{
+    const int f = threadIdx.x;
+    if (f >= MLP_IN) return;
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += partials[(int64_t)b * MLP_IN + f];
+    out[f] = t / div;
+}
+
+// Minibatch of `batch` rows of (X, y) drawn uniformly with replacement: row of draw b at step `step` is
+// floor(r N / 2^32), r the first word of Philox4x32-10 at counter (b mod 2^32, b >> 32, step, 0x6D6C7000),
+// key (seed mod 2^32, seed >> 32).
+__global__ void draw_batch_rows(const float *X, const float *y, int64_t N, int64_t batch, uint32_t k0, uint32_t k1,
+                                uint32_t step, float *Xb, float *yb)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    const U4 o = philox10(U4{(uint32_t)b, (uint32_t)(b >> 32), step, 0x6D6C7000u}, k0, k1);
+    const int64_t i = (int64_t)(((uint64_t)o.x * (uint64_t)N) >> 32);
+    const float4 *src = reinterpret_cast<const float4 *>(X + i * MLP_IN);
+    float4 *dst = reinterpret_cast<float4 *>(Xb + b * MLP_IN);
+    dst[0] = src[0];
+    dst[1] = src[1];
+    yb[b] = y[i];
+}
+
 template <typename real>
 static sme_status features_t(sme_op op, uint64_t seed, float *rowF, float *colF, cudaStream_t s)
 {
@@ -548,6 +607,56 @@ extern "C" sme_status sme_mlp_train_step(sme_mlp M, const float *X, const float 
     const float c1 = 1.f / (1.f - std::pow(b1, (float)m.adam_t)), c2 = 1.f / (1.f - std::pow(b2, (float)m.adam_t));
     mlp_adam<<<nblk(P_COUNT), 256, 0, (cudaStream_t)stream>>>(m.master, m.wbf, m.m1, m.m2, m.grad, lr, b1, b2, 1e-8f,
                                                               c1, c2);
+    SME_CUDA(cudaGetLastError());
+    return SME_OK;
+}
+
+extern "C" sme_status sme_mlp_fit_normalisation(sme_mlp M, const float *X, int64_t N, void *stream)
+{
+    if (!M || !X || N < 2) {
+        set_error("sme_mlp_fit_normalisation: a network and at least two feature rows are required");
+        return SME_ERR_ARG;
+    }
+    if ((uintptr_t)X % 16) {
+        set_error("sme_mlp_fit_normalisation: X must be 16-byte aligned");
+        return SME_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    AsyncScratch scratch(s);
+    SME_CUDA(scratch.alloc((size_t)(NORM_BLOCKS + 2) * MLP_IN * sizeof(double)));
+    double *partials = scratch.as<double>(), *mean = partials + NORM_BLOCKS * MLP_IN, *var = mean + MLP_IN;
+    feature_sums<<<NORM_BLOCKS, NORM_THREADS, 0, s>>>(X, N, nullptr, 0, partials);
+    feature_finish<<<1, 32, 0, s>>>(partials, NORM_BLOCKS, (double)N, mean);
+    feature_sums<<<NORM_BLOCKS, NORM_THREADS, 0, s>>>(X, N, mean, 1, partials);
+    feature_finish<<<1, 32, 0, s>>>(partials, NORM_BLOCKS, (double)(N - 1), var);
+    SME_CUDA(cudaGetLastError());
+    double h[2 * MLP_IN];
+    SME_CUDA(cudaMemcpyAsync(h, mean, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SME_CUDA(cudaStreamSynchronize(s));
+    float norm[2 * MLP_IN];
+    for (int f = 0; f < MLP_IN; ++f) {
+        const double sd = std::sqrt(h[MLP_IN + f]);
+        norm[f] = (float)h[f];
+        norm[MLP_IN + f] = sd > 1e-6 ? (float)sd : 1.f;  // constant features are left unscaled
+    }
+    return sme_mlp_set_params(M, nullptr, norm);
+}
+
+extern "C" sme_status sme_mlp_draw_batch(const float *X, const float *target, int64_t N, int64_t batch, uint64_t seed,
+                                         int64_t step, float *X_batch, float *target_batch, void *stream)
+{
+    if (!X || !target || !X_batch || !target_batch || N < 1 || N > 0xffffffffLL || batch < 0 || step < 0) {
+        set_error("sme_mlp_draw_batch: bad arguments");
+        return SME_ERR_ARG;
+    }
+    if ((uintptr_t)X % 16 || (uintptr_t)X_batch % 16) {
+        set_error("sme_mlp_draw_batch: feature arrays must be 16-byte aligned");
+        return SME_ERR_ARG;
+    }
+    if (batch == 0) return SME_OK;
+    draw_batch_rows<<<nblk(batch), 256, 0, (cudaStream_t)stream>>>(X, target, N, batch, (uint32_t)seed,
+                                                                   (uint32_t)(seed >> 32), (uint32_t)step, X_batch,
+                                                                   target_batch);
     SME_CUDA(cudaGetLastError());
     return SME_OK;
 }

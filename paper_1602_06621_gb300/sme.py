@@ -140,6 +140,8 @@ SIGNATURES = {
     "sme_batch_warm_start": ([_vp, _vp, _u64, _vp, _vp, _vp], _i32),
     "sme_op_norm2": ([_vp, _vp, _vp, _i32, ctypes.POINTER(ctypes.c_double), _vp], _i32),
     "sme_ccp_lasso": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp], _i32),
+    "sme_mlp_fit_normalisation": ([_vp, _vp, _i64, _vp], _i32),
+    "sme_mlp_draw_batch": ([_vp, _vp, _i64, _i64, _u64, _i64, _vp, _vp, _vp], _i32),
     "sme_op_create_csr_shard": ([ctypes.POINTER(_vp), _i64, _i64, _i64, _vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp],
                                 _i32),
     "sme_shard_get_info": ([_vp, _i32, ctypes.POINTER(sme_shard_info)], _i32),
@@ -548,6 +550,18 @@ def sme_mlp_train_step(mlp, X, target, lr, stream=None, want_loss=False):
     _check(load().sme_mlp_train_step(mlp, _ptr(X), _ptr(target), int(X.shape[0]), float(lr),
                                      ctypes.byref(loss) if want_loss else None, _stream(stream)), "sme_mlp_train_step")
     return loss.value if want_loss else None
+
+
+def sme_mlp_fit_normalisation(mlp, X, stream=None):
+    """Set a network's input normalisation to the mean and deviation of the feature rows X (CUDA tensor)."""
+    _check(load().sme_mlp_fit_normalisation(mlp, _ptr(X), int(X.shape[0]), _stream(stream)),
+           "sme_mlp_fit_normalisation")
+
+
+def sme_mlp_draw_batch(X, target, batch, seed, step, X_batch, target_batch, stream=None):
+    """Fill (X_batch, target_batch) with `batch` rows of (X, target) drawn with replacement (library kernel)."""
+    _check(load().sme_mlp_draw_batch(_ptr(X), _ptr(target), int(X.shape[0]), int(batch), int(seed), int(step),
+                                     _ptr(X_batch), _ptr(target_batch), _stream(stream)), "sme_mlp_draw_batch")
 
 
 def sme_op_features(op, seed, row_features, col_features, stream=None):

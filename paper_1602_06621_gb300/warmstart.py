@@ -64,19 +64,18 @@ def training_set(mats, **kw):
 
 
 def train(mlp, X, y, *, steps=600, batch=8192, lr=2e-3, seed=0):
-    """Set the input normalisation from X, then `steps` minibatch Adam steps; returns the loss history."""
+    """Fit the input normalisation to X, then `steps` minibatch Adam steps (minibatches drawn by the library,
+    with replacement); returns the loss history."""
     import torch
-    mean = X.mean(0).cpu().numpy()
-    std = X.std(0).cpu().numpy()
-    std = np.where(std > 1e-6, std, 1.0)
-    sme.sme_mlp_set_params(mlp, norm=np.concatenate([mean, std]).astype(np.float32))
-    g = torch.Generator(device="cuda")
-    g.manual_seed(seed)
-    hist = []
+    X, y = X.contiguous(), y.contiguous()
+    sme.sme_mlp_fit_normalisation(mlp, X)
     N = X.shape[0]
+    nb = min(batch, N)
+    Xb = torch.empty((nb, FEATURES), dtype=torch.float32, device=X.device)
+    yb = torch.empty(nb, dtype=torch.float32, device=X.device)
+    hist = []
     for step in range(steps):
-        idx = torch.randint(0, N, (min(batch, N),), device="cuda", generator=g)
-        Xb, yb = X[idx].contiguous(), y[idx].contiguous()
+        sme.sme_mlp_draw_batch(X, y, nb, seed, step, Xb, yb)
         want = step % 50 == 0 or step == steps - 1
         loss = sme.sme_mlp_train_step(mlp, Xb, yb, lr * (0.5 ** (step / max(1, steps // 3))), want_loss=want)
         if want:

@@ -264,3 +264,47 @@ def test_batch_evaluate_matches_single_operators():
         f = O.objective(A, u[ro[i]:ro[i + 1]].astype(np.float64), v[co[i]:co[i + 1]].astype(np.float64),
                         alpha=d["alpha"], beta=d["beta"], gamma=0.01)
         assert got[i]["objective"] == pytest.approx(f, rel=1e-9)
+
+
+def test_fit_normalisation_matches_numpy():
+    """Per-feature mean and deviation (N - 1) of the training features, summed on the device in FP64; a constant
+    feature keeps scale 1."""
+    rng = np.random.default_rng(12)
+    N = 100003
+    X = rng.normal(0, 1, (N, OM.IN)) * np.exp(rng.normal(0, 2, OM.IN)) + rng.normal(0, 5, OM.IN)
+    X[:, 3] = 2.5  # constant
+    X = X.astype(np.float32)
+    mlp = S.sme_mlp_create(1)
+    try:
+        S.sme_mlp_fit_normalisation(mlp, torch.tensor(X, device="cuda"))
+        nrm = S.sme_mlp_get_params(mlp)[1]
+    finally:
+        S.sme_mlp_destroy(mlp)
+    X64 = X.astype(np.float64)
+    mean, std = X64.mean(0), X64.std(0, ddof=1)
+    std[3] = 1.0
+    np.testing.assert_allclose(nrm[:OM.IN], mean.astype(np.float32), rtol=1e-6, atol=1e-6 * np.abs(mean).max())
+    np.testing.assert_allclose(nrm[OM.IN:], std.astype(np.float32), rtol=1e-6)
+
+
+def test_draw_batch_rows_follow_the_documented_generator():
+    """Minibatch rows drawn by the library are the rows the documented Philox counter layout names
+    (row floor(r N / 2^32), r = first word at counter (b, b >> 32, step, 0x6D6C7000)), copied exactly."""
+    rng = np.random.default_rng(13)
+    N, batch, seed = 77777, 5000, 0x1234_5678_9ABC
+    X = rng.normal(0, 1, (N, OM.IN)).astype(np.float32)
+    y = rng.normal(0, 1, N).astype(np.float32)
+    Xd, yd = torch.tensor(X, device="cuda"), torch.tensor(y, device="cuda")
+    Xb = torch.zeros((batch, OM.IN), device="cuda")
+    yb = torch.zeros(batch, device="cuda")
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for step in (0, 7):
+        S.sme_mlp_draw_batch(Xd, yd, batch, seed, step, Xb, yb)
+        got_X, got_y = Xb.cpu().numpy(), yb.cpu().numpy()
+        for b in (0, 1, 2, 999, 4999):
+            r = int(O.philox4x32_10([b, 0, step, 0x6D6C7000], key)[0])
+            i = (r * N) >> 32
+            np.testing.assert_array_equal(got_X[b], X[i])
+            assert got_y[b] == y[i]
+        # draws with replacement: about batch^2 / (2 N) = 160 repeats are expected among 5000
+        assert np.unique(got_y).size > 0.9 * batch
