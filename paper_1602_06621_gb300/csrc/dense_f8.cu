@@ -27,6 +27,7 @@
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "sme_internal.cuh"
@@ -159,6 +160,42 @@ __device__ __forceinline__ float f8_next_bound(const DenseArgs8 &a, int side)
 }
 
 // EXPIRE: the instantiation for the test of the timeout path (see dense.cu).
+// Remote arrive (release, cluster scope) on an mbarrier given by its cluster-window address.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+
+// Work item w of a launch: the products' 256-row pair tiles, the forward product's first.  This CTA's tile
+// is tile 2p + rank of its side; with an odd tile count the second CTA of the last pair repeats its
+// partner's tile and writes nothing.
+struct F8Item {
+    bool cols, active;
+    int tile, nk;
+};
+
+__device__ __forceinline__ F8Item f8_item(const DenseArgs8 &a, int w, uint32_t crank)
+{
+    F8Item it;
+    const int row_pairs = (a.row_tiles + 1) / 2;
+    it.cols = w >= row_pairs;
+    const int p = it.cols ? w - row_pairs : w;
+    const int ntiles = it.cols ? a.col_tiles : a.row_tiles;
+    const int t = 2 * p + (int)crank;
+    it.active = t < ntiles;
+    it.tile = it.active ? t : ntiles - 1;
+    it.nk = (int)((it.cols ? a.m : a.n) / F8_BK);
+    return it;
+}
+
+// Persistent: cluster c of the grid takes work items c, c + clusters, ...  TMEM holds two accumulators of KP
+// columns, so the epilogue of one item overlaps the copies and MMAs of the next; the ring of K-blocks runs on
+// across items.  Barriers: full / empty per ring slot (copies -> MMAs -> slot free), acc_full[2] (the
+// leader's commit after an item's MMAs, in both CTAs), acc_empty[2] (in the leader: one arrival per epilogue
+// warp of the pair once it has read the accumulator), mma_done (after the issuer's last MMA: TMEM may be
+// freed).  Every wait is bounded; a role that gives up sets ST_TIMEOUT, and the issuer then still walks the
+// accumulator protocol (without MMAs) so that every epilogue wait ends and no barrier skips a phase.
+// EXPIRE: the instantiation for the test of the timeout path (see dense.cu).
 template <int KP, bool EXPIRE = false>
 __global__ void __launch_bounds__(F8_THREADS, 1) dense_iteration_f8(const __grid_constant__ DenseMaps8 maps, DenseArgs8 a)
 {
@@ -169,28 +206,25 @@ __global__ void __launch_bounds__(F8_THREADS, 1) dense_iteration_f8(const __grid
     constexpr uint16_t PAIR = 0x3;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ uint64_t full[NS], empty[NS], acc_bar;
+    __shared__ uint64_t full[NS], empty[NS], acc_full[2], acc_empty[2], mma_done;
     __shared__ uint32_t tmem_base_sh;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool cols = (int)blockIdx.x >= a.row_ctas;
-    const int idx = cols ? (int)blockIdx.x - a.row_ctas : (int)blockIdx.x;
-    const int ntiles = cols ? a.col_tiles : a.row_tiles;
-    const bool active = idx < ntiles;
-    const int tile = active ? idx : ntiles - 1;
     const uint32_t crank = cluster_rank();
     const bool leader = crank == 0;
-    const int64_t K = cols ? a.m : a.n;
-    const int nk = (int)(K / F8_BK);
-    const CUtensorMap *mapX = cols ? &maps.X[1] : &maps.X[0];
-    const CUtensorMap *mapB = cols ? &maps.B[1] : &maps.B[0];
+    const int cluster = (int)blockIdx.x / 2, nclusters = (int)gridDim.x / 2;
+    const int nitems = (a.row_tiles + 1) / 2 + (a.col_tiles + 1) / 2;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&acc_bar, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 8);  // four epilogue warps in each CTA of the pair
+        }
+        mbar_init(&mma_done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         if (blockIdx.x == 0 && a.mode == 0) {
             a.q_clear[0] = 0u;  // the slot the next iteration fills (nothing reads it in this launch)
@@ -199,7 +233,7 @@ __global__ void __launch_bounds__(F8_THREADS, 1) dense_iteration_f8(const __grid
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                     "r"((uint32_t)KP));
+                     "r"((uint32_t)(2 * KP)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -208,119 +242,151 @@ __global__ void __launch_bounds__(F8_THREADS, 1) dense_iteration_f8(const __grid
     const uint32_t tmem = tmem_base_sh;
 
     if (warp == 0 && lane == 0) {
-        // TMA producer (both CTAs): per K-block this CTA's 128 rows of X and its KP/2 operand rows into one
-        // slot; completion counted on the leader's full barrier.
+        // TMA producer (both CTAs): the K-blocks of this cluster's items through one continuous ring; per
+        // K-block this CTA's 128 rows of X and its KP/2 operand rows, counted on the leader's full barrier.
         bool bad = false;
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % NS;
-            if (kb >= NS && !mbar_wait_n(&empty[s], ((kb / NS) - 1) & 1, PIPE_LIMIT)) {
-                bad = true;
-                break;
+        uint32_t g = 0;  // K-blocks issued so far
+        for (int w = cluster; w < nitems && !bad; w += nclusters) {
+            const F8Item it = f8_item(a, w, crank);
+            const CUtensorMap *mapX = it.cols ? &maps.X[1] : &maps.X[0];
+            const CUtensorMap *mapB = it.cols ? &maps.B[1] : &maps.B[0];
+            for (int kb = 0; kb < it.nk; ++kb, ++g) {
+                const uint32_t s = g % NS;
+                if (g >= NS && !mbar_wait_n(&empty[s], ((g / NS) - 1) & 1, PIPE_LIMIT)) {
+                    bad = true;
+                    break;
+                }
+                if (leader) mbar_expect_tx(&full[s], 2 * C::SLOT);
+                uint8_t *slot = smem + s * C::SLOT;
+                const uint32_t bar = cluster_addr(&full[s], 0);
+                tma_load_2d_pair(slot, mapX, 0, (it.tile * it.nk + kb) * F8_BM, bar);
+                tma_load_2d_pair(slot + F8_A_SLOT, mapB, kb * F8_BK, (int)crank * (KP / 2), bar);
             }
-            if (leader) mbar_expect_tx(&full[s], 2 * C::SLOT);
-            uint8_t *slot = smem + s * C::SLOT;
-            const uint32_t bar = cluster_addr(&full[s], 0);
-            tma_load_2d_pair(slot, mapX, 0, (tile * nk + kb) * F8_BM, bar);
-            tma_load_2d_pair(slot + F8_A_SLOT, mapB, kb * F8_BK, (int)crank * (KP / 2), bar);
         }
         if (bad) atomicOr(a.status, ST_TIMEOUT);
     } else if (warp == 1 && lane == 0 && leader) {
-        // MMA issuer (leader only): four K = 32 MMAs (M = 256 over the pair, N = KP) per K-block.
+        // MMA issuer (leader only): per item, once the epilogue has released its accumulator, four K = 32 MMAs
+        // (M = 256 over the pair, N = KP) per K-block, then a commit that the accumulator is complete.
         const uint32_t sbase = smem_u32(smem);
-        bool bad = false;
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % NS;
-            if (!mbar_wait_n(&full[s], (kb / NS) & 1, PIPE_LIMIT)) {
-                bad = true;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint64_t ad0 = smem_desc_sw128_u32(sbase + (uint32_t)(s * C::SLOT));
-            const uint64_t bd0 = smem_desc_sw128_u32(sbase + (uint32_t)(s * C::SLOT + F8_A_SLOT));
+        bool bad = false, flagged = false;
+        uint32_t g = 0;
+        int itn = 0;
+        for (int w = cluster; w < nitems; w += nclusters, ++itn) {
+            const F8Item it = f8_item(a, w, 0);
+            const int buf = itn & 1;
+            if (itn >= 2 && !mbar_wait(&acc_empty[buf], ((itn / 2) - 1) & 1)) bad = true;
+            if (!bad) {
+                const uint32_t acc = tmem + (uint32_t)(buf * KP);
+                for (int kb = 0; kb < it.nk; ++kb, ++g) {
+                    const uint32_t s = g % NS;
+                    if (!mbar_wait_n(&full[s], (g / NS) & 1, PIPE_LIMIT)) {
+                        bad = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint64_t ad0 = smem_desc_sw128_u32(sbase + (uint32_t)(s * C::SLOT));
+                    const uint64_t bd0 = smem_desc_sw128_u32(sbase + (uint32_t)(s * C::SLOT + F8_A_SLOT));
 #pragma unroll
-            for (int kk = 0; kk < F8_BK / 32; ++kk)  // +32 bytes along K per step
-                mma_e4m3(tmem, ad0 + (uint64_t)(kk * 2), bd0 + (uint64_t)(kk * 2), IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
-            mma_commit_multicast(&empty[s], PAIR);
+                    for (int kk = 0; kk < F8_BK / 32; ++kk)  // +32 bytes along K per step
+                        mma_e4m3(acc, ad0 + (uint64_t)(kk * 2), bd0 + (uint64_t)(kk * 2), IDESC,
+                                 (kb > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit_multicast(&empty[s], PAIR);
+                }
+            }
+            if (bad && !flagged) {
+                atomicOr(a.status, ST_TIMEOUT);  // seen by the epilogues, which then write nothing
+                __threadfence();
+                flagged = true;
+            }
+            mma_commit_multicast(&acc_full[buf], PAIR);  // in both CTAs once this item's MMAs have completed
         }
-        if (bad) {
-            atomicOr(a.status, ST_TIMEOUT);
-            __threadfence();
-        }
-        mma_commit_multicast(&acc_bar, PAIR);
+        mma_commit_multicast(&mma_done, PAIR);
     }
 
     if (warp >= 2) {
-        const bool ok = mbar_wait(&acc_bar, 0);
-        if (!ok) atomicOr(a.status, ST_TIMEOUT);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // Epilogue: warps 2..5, one TMEM lane (one row of the tile) per thread.
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
-        const int64_t r = (int64_t)tile * F8_BM + row;
-        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16);
-        float ss = 0.f;
+        int itn = 0;
+        for (int w = cluster; w < nitems; w += nclusters, ++itn) {
+            const F8Item it = f8_item(a, w, crank);
+            const int buf = itn & 1;
+            const bool ok = mbar_wait(&acc_full[buf], (itn / 2) & 1);
+            if (!ok) atomicOr(a.status, ST_TIMEOUT);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t taddr = tmem + (uint32_t)(buf * KP) + ((uint32_t)(quad * 32) << 16);
+            float ss = 0.f;
 #pragma unroll 1
-        for (int c = 0; c < KP / 32; ++c) {
-            float y[32];
-            tmem_ld32(taddr + c * 32, y);
+            for (int c = 0; c < KP / 32; ++c) {
+                float y[32];
+                tmem_ld32(taddr + c * 32, y);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) ss += y[i] * y[i];
-        }
-        const int side = cols ? 1 : 0;
-        uint32_t qkey = 0u;
-        if (ok && active && !(*(volatile int *)a.status & ST_TIMEOUT)) {
-            float *X = a.x[side];
-            const float xo = X[r];
-            const float ex = expf(xo);
-            const float ci = (!cols && a.row_scale) ? a.row_scale[r] : 1.f;
-            // The accumulators carry the other side's operand scale 2^S twice after squaring.
-            const float z = ex * ex * ci * ci * ldexpf(ss, -2 * a.s_cur[1 - side]) * (1.f / (float)KP);
-            if (a.mode == 1) {
-                a.z[side][r] = z;
-            } else {
-                float xn = xo - a.eta * (z - a.target2[side] + a.gamma * xo);
-                if (!isfinite(xn)) atomicOr(a.status, ST_NONFINITE);
-                xn = fminf(fmaxf(xn, -a.M), a.M);
-                X[r] = xn;
-                float *XB = a.xb[side];
-                XB[r] = a.avg_new * xn + a.avg_old * XB[r];
-                const int S = f8_scale_exp_log(f8_next_bound(a, side));
-                const uint8_t mag = f8_code(ldexpf(expf(xn) * ci, S));
-                qkey = f8_key(xn + logf(fabsf(ci)));
-                const int64_t ld = cols ? a.n : a.m;
-                uint8_t *Bn = a.bnext[side];
-                for (int g = 0; g < KP / 128; ++g) {
-                    const U4 o = philox10(U4{(uint32_t)r, a.t_next, a.sid_out[side], (uint32_t)g}, a.key0, a.key1);
-                    const uint32_t words[4] = {o.x, o.y, o.z, o.w};
+                for (int i = 0; i < 32; ++i) ss += y[i] * y[i];
+            }
+            // The accumulator is in registers: release it to the issuer for the item after next.
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(cluster_addr(&acc_empty[buf], 0));
+            const bool cols = it.cols;
+            const int side = cols ? 1 : 0;
+            const int64_t r = (int64_t)it.tile * F8_BM + row;
+            uint32_t qkey = 0u;
+            if (ok && it.active && !(*(volatile int *)a.status & ST_TIMEOUT)) {
+                float *X = a.x[side];
+                const float xo = X[r];
+                const float ex = expf(xo);
+                const float ci = (!cols && a.row_scale) ? a.row_scale[r] : 1.f;
+                // The accumulators carry the other side's operand scale 2^S twice after squaring.
+                const float z = ex * ex * ci * ci * ldexpf(ss, -2 * a.s_cur[1 - side]) * (1.f / (float)KP);
+                if (a.mode == 1) {
+                    a.z[side][r] = z;
+                } else {
+                    float xn = xo - a.eta * (z - a.target2[side] + a.gamma * xo);
+                    if (!isfinite(xn)) atomicOr(a.status, ST_NONFINITE);
+                    xn = fminf(fmaxf(xn, -a.M), a.M);
+                    X[r] = xn;
+                    float *XB = a.xb[side];
+                    XB[r] = a.avg_new * xn + a.avg_old * XB[r];
+                    const int S = f8_scale_exp_log(f8_next_bound(a, side));
+                    const uint8_t mag = f8_code(ldexpf(expf(xn) * ci, S));
+                    qkey = f8_key(xn + logf(fabsf(ci)));
+                    const int64_t ld = cols ? a.n : a.m;
+                    uint8_t *Bn = a.bnext[side];
+                    for (int gg = 0; gg < KP / 128; ++gg) {
+                        const U4 o = philox10(U4{(uint32_t)r, a.t_next, a.sid_out[side], (uint32_t)gg}, a.key0, a.key1);
+                        const uint32_t words[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll 8
-                    for (int p = 0; p < 128; ++p) {
-                        const uint32_t neg = (words[p >> 5] >> (p & 31)) & 1u;
-                        Bn[(int64_t)(g * 128 + p) * ld + r] = (uint8_t)(mag ^ (neg << 7));
+                        for (int p = 0; p < 128; ++p) {
+                            const uint32_t neg = (words[p >> 5] >> (p & 31)) & 1u;
+                            Bn[(int64_t)(gg * 128 + p) * ld + r] = (uint8_t)(mag ^ (neg << 7));
+                        }
                     }
                 }
             }
-        }
-        if (a.mode == 0) {
-            qkey = __reduce_max_sync(0xffffffffu, qkey);
-            if (lane == 0 && qkey) atomicMax(&a.q_cur[cols ? 1 : 0], qkey);
-            if (blockIdx.x == 0 && threadIdx.x == 64) {
-                a.s_next[0] = f8_scale_exp_log(f8_next_bound(a, 0));
-                a.s_next[1] = f8_scale_exp_log(f8_next_bound(a, 1));
+            if (a.mode == 0) {
+                qkey = __reduce_max_sync(0xffffffffu, qkey);
+                if (lane == 0 && qkey) atomicMax(&a.q_cur[side], qkey);
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (a.mode == 0 && blockIdx.x == 0 && threadIdx.x == 64) {
+            a.s_next[0] = f8_scale_exp_log(f8_next_bound(a, 0));
+            a.s_next[1] = f8_scale_exp_log(f8_next_bound(a, 1));
+        }
     }
     __syncthreads();
     if (warp == 1) {
-        if (lane == 0) mbar_wait(&acc_bar, 0);
+        // Every MMA must have completed before TMEM is released (bounded; immediate normally).
+        if (lane == 0) mbar_wait(&mma_done, 0);
         __syncwarp();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)KP));
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * KP)));
     }
+    // Neither CTA leaves while copies, commits or arrivals of the pair may still target its shared memory;
+    // after an abandoned wait anywhere, copies already issued are given time to land.
     cluster_sync();
     if (threadIdx.x == 0 && (*(volatile int *)a.status & ST_TIMEOUT))
         for (int i = 0; i < 2000; ++i) __nanosleep(1000);
 }
-
 // ------------------------------------------------------------------ set-up kernels
 
 // Maxima of one side's operand over a state vector: key of max (x_i + log|c_i|) and max |e^{x_i} c_i|.
@@ -525,7 +591,15 @@ static sme_status run_f8(sme_op op, const DenseArgs8 &a, int buf, cudaStream_t s
     maps.X[1] = D->mapAt8;
     maps.B[0] = D->mapBf8[buf];
     maps.B[1] = D->mapBb8[buf];
-    const int grid = a.row_ctas + ((a.col_tiles + 1) & ~1);
+    // Persistent clusters of two CTAs: one per SM pair, at most one per work item.
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        SME_CUDA(cudaGetDevice(&dev));
+        SME_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int items = (a.row_tiles + 1) / 2 + (a.col_tiles + 1) / 2;
+    const int grid = 2 * std::max(1, std::min(items, sms / 2));
     if (a.pipe_limit == 0) {
         if (a.kp == 256) return launch_f8<256, true>(maps, a, grid, s);
         return launch_f8<128, true>(maps, a, grid, s);
