@@ -115,3 +115,29 @@ def test_split_part_refuses_whole_matrix_calls():
         assert ei.value.name == "SME_ERR_UNSUPPORTED"
     finally:
         sme.sme_op_destroy(op)
+
+
+@pytest.mark.parametrize("P,k", [(5, 64), (23, 2), (1, 8)])
+def test_split_matrix_edge_shapes_equal_unsplit(P, k):
+    """37 x 23 with empty rows and columns, FP64: parts down to one column each (P = n = 23), 16-byte table
+    entries (k = 64), and the trivial split (P = 1); T = 8 from zero, bit for bit against the unsplit run."""
+    import torch
+    A = I.sparse_uniform_density(37, 23, 0.08, seed=5)
+    T = 8
+    op = sme.sme_op_create_csr(A.m, A.n, A.row_ptr, A.col_idx, A.vals)
+    try:
+        z = [torch.zeros(x, dtype=torch.float64, device="cuda") for x in (A.m, A.n, A.m, A.n)]
+        sme.sme_equilibrate(op, *z, T=T, k=k, seed=6, t0=20)
+        ref = [x.cpu().numpy() for x in z]
+    finally:
+        sme.sme_op_destroy(op)
+    parts = _parts(A, P, k, torch.float64)
+    try:
+        if k > 32:
+            assert parts[0].info["entry_bytes"] == 16
+        SH.run(parts, SH.LocalExchange(), T=T, k=k, seed=6, t0=20)
+        got = _gather(parts, A)
+    finally:
+        _destroy(parts)
+    for g, r in zip(got, ref):
+        np.testing.assert_array_equal(g, r)
