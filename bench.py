@@ -82,6 +82,17 @@ def dense_f8_source_hash():
     h.update(_section(KERNEL_HEADER, b"Philox4x32-10", b"------ operator"))
     return h.hexdigest()
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sgd_iteration_f32_k32_large.txt")
+BATCHED_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sgd_iteration_f32_k16_batched.txt")
+BATCH_LAYOUT_SOURCES = [os.path.join(ROOT, "paper_1602_06621_gb300", "csrc", f) for f in ("batch.cu", "build_kernels.cu")]
+
+
+def batched_source_hash():
+    """The iteration kernel's device code plus the sources that lay a batch out in HBM (matrix groups, slice
+    order), which decide how many of its gathers hit L1 and so its DRAM traffic."""
+    h = hashlib.sha256(kernel_source_hash().encode())
+    for path in BATCH_LAYOUT_SOURCES:
+        h.update(open(path, "rb").read())
+    return h.hexdigest()
 # Random 8-byte gathers per second from L2-resident tables, measured on GB300 by a random-gather
 # microbenchmark (figures in profiles/sgd_iteration_f32_k32_large.txt): the second ceiling of the sparse
 # kernels, which gather one table entry per nonzero per pass.
@@ -661,7 +672,9 @@ def batched_line(args, rank, world, local, mats=None):
                    "matrices": count, "rows": M, "cols": N, "nnz": nnz, "k": k, "T": T,
                    "launch_shape": tuned, "l2": f"inputs larger than L2 ({16 * nnz / 1e6:.0f} MB per iteration)"},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                     "traffic": None, "peak_kind": kind, "kernel": "sgd_iteration<float,16> over the batch",
+                     "traffic": recorded_traffic(BATCHED_TRAFFIC_FILE, batched_source_hash) if args.scale == 1.0 else None,
+                     "traffic_kind": "ncu DRAM bytes of one full-size launch (profiles/sgd_iteration_f32_k16_batched.txt)",
+                     "peak_kind": kind, "kernel": "sgd_iteration<float,16> over the batch",
                      "algorithmic_bytes_per_launch": bytes_iter, "launch_us": iter_s * 1e6, "gather_ceiling": gather_roofline(nnz, iter_s)},
         "gpu_launches": (T + 4) * args.steps, "clocks": clk.summary(),
         "quality": {"spread_median": float(np.median(spreads)), "spread_max": float(spreads.max()),
