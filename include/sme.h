@@ -496,10 +496,12 @@ sme_status sme_shard_get_info(sme_op op, int32_t k, sme_shard_info *info);
  * state (state type); p as for sme_equilibrate (alpha, beta default from the whole matrix's m, n). */
 sme_status sme_shard_begin(sme_op op, const sme_equil_params *p, const void *u, const void *v, const void *u_bar,
                            const void *v_bar, void *row_table, void *col_table, void *stream);
-/* Iteration t: reads the whole current tables, writes this part's chunks of the next ones (other buffers). */
+/* Iteration t: reads the whole current tables, writes this part's chunks of the next ones (other buffers).
+ * SME_ERR_ARG, with nothing launched, before a successful sme_shard_begin on this op or when p->k needs table
+ * entries of another size than the k given to sme_shard_begin (the tables are sized for one entry size). */
 sme_status sme_shard_step(sme_op op, const sme_equil_params *p, int32_t t, const void *row_table_in,
                           const void *col_table_in, void *row_table_out, void *col_table_out, void *stream);
-/* This part's u, v, u_bar, v_bar after the last step. */
+/* This part's u, v, u_bar, v_bar after the last step (SME_ERR_ARG before a successful sme_shard_begin). */
 sme_status sme_shard_end(sme_op op, void *u, void *v, void *u_bar, void *v_bar, void *stream);
 
 /* ------------------------------------------------------------------ allocation-free estimator */

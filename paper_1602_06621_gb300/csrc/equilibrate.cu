@@ -1258,17 +1258,34 @@ extern "C" sme_status sme_shard_begin(sme_op op, const sme_equil_params *p, cons
         set_error("sme_shard_begin: null pointer");
         return SME_ERR_ARG;
     }
-    if (op->dbl)
-        return shard_begin_t<double>(op, p, (const double *)u, (const double *)v, (const double *)u_bar,
-                                     (const double *)v_bar, row_table, col_table, (cudaStream_t)stream);
-    return shard_begin_t<float>(op, p, (const float *)u, (const float *)v, (const float *)u_bar, (const float *)v_bar,
-                                row_table, col_table, (cudaStream_t)stream);
+    op->shard->begun_kw = 0;
+    const sme_status st =
+        op->dbl ? shard_begin_t<double>(op, p, (const double *)u, (const double *)v, (const double *)u_bar,
+                                        (const double *)v_bar, row_table, col_table, (cudaStream_t)stream)
+                : shard_begin_t<float>(op, p, (const float *)u, (const float *)v, (const float *)u_bar,
+                                       (const float *)v_bar, row_table, col_table, (cudaStream_t)stream);
+    if (st == SME_OK) op->shard->begun_kw = (p->k + 31) / 32;
+    return st;
+}
+
+// A step or the end needs the state a successful sme_shard_begin set up; a step also needs table entries of
+// the size that begin wrote (the tables are sized by the caller from sme_shard_get_info for one k).
+static sme_status shard_begun(sme_op op, int k, const char *where)
+{
+    const int kw = k > 0 ? (k + 31) / 32 : op->shard->begun_kw;
+    if (op->shard->begun_kw == 0 || !op->ws.u || !op->ws.v || !op->ws.ub || !op->ws.vb ||
+        entry_bytes(op->dbl, kw) != entry_bytes(op->dbl, op->shard->begun_kw)) {
+        set_error("%s: call sme_shard_begin first, with a k of the same table entry size", where);
+        return SME_ERR_ARG;
+    }
+    return SME_OK;
 }
 
 extern "C" sme_status sme_shard_step(sme_op op, const sme_equil_params *p, int32_t t, const void *row_table_in,
                                      const void *col_table_in, void *row_table_out, void *col_table_out, void *stream)
 {
     SME_TRY(shard_args(op, p, "sme_shard_step"));
+    SME_TRY(shard_begun(op, p->k, "sme_shard_step"));
     if (t < 1 || !row_table_in || !col_table_in || !row_table_out || !col_table_out || row_table_in == row_table_out ||
         col_table_in == col_table_out) {
         set_error("sme_shard_step: bad iteration or tables (the next tables must be other buffers)");
@@ -1282,10 +1299,11 @@ extern "C" sme_status sme_shard_step(sme_op op, const sme_equil_params *p, int32
 
 extern "C" sme_status sme_shard_end(sme_op op, void *u, void *v, void *u_bar, void *v_bar, void *stream)
 {
-    if (!op || !op->shard || !u || !v || !u_bar || !v_bar || !op->ws.u) {
-        set_error("sme_shard_end: bad arguments (call sme_shard_begin first)");
+    if (!op || !op->shard || !u || !v || !u_bar || !v_bar) {
+        set_error("sme_shard_end: bad arguments");
         return SME_ERR_ARG;
     }
+    SME_TRY(shard_begun(op, 0, "sme_shard_end"));
     cudaStream_t s = (cudaStream_t)stream;
     const ShardInfo &I = *op->shard;
     if (op->dbl) {

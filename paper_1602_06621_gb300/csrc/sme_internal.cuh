@@ -187,6 +187,7 @@ struct ShardInfo {
     int64_t gm = 0, gn = 0, gnnz = 0;       // the whole matrix
     int64_t r0 = 0, r1 = 0, c0 = 0, c1 = 0;  // this part's rows [r0, r1) and columns [c0, c1)
     int64_t rchunk = 0, cchunk = 0;          // table entries per part (the largest block)
+    int32_t begun_kw = 0;                    // probe words per table entry of the last sme_shard_begin (0: none)
 };
 
 // A batch of matrices held as one block-diagonal operator (batch.cu).

@@ -141,3 +141,30 @@ def test_split_matrix_edge_shapes_equal_unsplit(P, k):
         _destroy(parts)
     for g, r in zip(got, ref):
         np.testing.assert_array_equal(g, r)
+
+
+def test_split_part_refuses_steps_without_a_matching_begin():
+    """A step or an end before sme_shard_begin, or a step whose k needs another table entry size than the
+    begin's, is refused on the host (the tables were sized for one entry size); nothing is launched."""
+    import torch
+    A = I.workload_large(scale=0.001, seed=3)
+    op = sme.sme_op_create_csr_shard(A.m, A.n, A.row_ptr, A.col_idx, A.vals, 2, 0)
+    try:
+        p8 = SH.Part(op, 8, "cuda")
+        with pytest.raises(sme.SmeError) as ei:
+            p8.step(1, 1, dict(T=1, k=8, t_begin=1))
+        assert ei.value.name == "SME_ERR_ARG"
+        with pytest.raises(sme.SmeError) as ei:
+            p8.end()
+        assert ei.value.name == "SME_ERR_ARG"
+        for tab in p8.tables.row + p8.tables.col:
+            tab.zero_()  # the other part's chunks are never written here
+        p8.begin(1, dict(T=1, k=8, t_begin=1))
+        with pytest.raises(sme.SmeError) as ei:
+            p8.step(1, 1, dict(T=1, k=64, t_begin=1))  # 16-byte entries into 8-byte tables
+        assert ei.value.name == "SME_ERR_ARG"
+        p8.step(1, 1, dict(T=1, k=16, t_begin=1))  # same entry size: accepted
+        p8.end()
+        torch.cuda.synchronize()
+    finally:
+        sme.sme_op_destroy(op)
