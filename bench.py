@@ -688,6 +688,13 @@ def batched_line(args, rank, world, local, mats=None):
 # ------------------------------------------------------------------------------------------ our arm
 
 def run_learned(args, rank, world, local):
+    line = learned_line(args, rank, world, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def learned_line(args, rank, world, local):
     """The learned warm start on the batched family (m log-uniform in [1e3, 2e4 * scale]).
 
     Training: 300 matrices labelled with the scalings Algorithm 1 converges to (gamma = 0.1, T = 400,
@@ -820,6 +827,7 @@ def run_learned(args, rank, world, local):
     p1.synchronize()
     pits = np.array([r["iters"] for r in pl])
     warm = out[f"warm start, t0={t0}"]
+    line = None
     if rank == 0:
         line = {
             "metric": "learned warm start: wall-time to row/column norm spread <= 1.05 (gamma 1e-3), "
@@ -841,13 +849,19 @@ def run_learned(args, rank, world, local):
                            "iters_max": int(pits.max()), "converged": int(sum(r["converged"] for r in pl)),
                            "iteration_cap": 20000},
         }
-        print(json.dumps(line), flush=True)
     sme.sme_mlp_destroy(mlp)
     sme.sme_batch_destroy(b)
-    return 0
+    return line
 
 
 def run_ccp(args, rank, world, local):
+    line = ccp_line(args, rank, world, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def ccp_line(args, rank, world, local):
     """Section 5.2's experiment: A as in Section 4 (1% uniform-random nonzeros, N(0,1) values, row and column
     factors e^{N(1,1)}) with m = 1e4, n = 2e4; x_hat with n/10 N(0,1) nonzeros, b = A x_hat + N(0,1) noise,
     lam = 1e-3 ||A^T b||_inf.  CCP (FP32 vectors, FP64 objective checks) without equilibration and after
@@ -891,24 +905,25 @@ def run_ccp(args, rank, world, local):
     pstar = min(long_hist + [long_res["objective"]])
     drift = (long_hist[-6] - long_hist[-1]) / long_res["objective0"] if len(long_hist) > 6 else None
     arms = {}
-    for T in (0, 10, 30, 100, 300):
-        def run():
-            ub, vb = equilibrate(op, T, f32)
-            x = torch.zeros(n, **f32)
-            return sme.sme_ccp_lasso(op, ub, vb, b32, x, lam=lam, max_iters=20000, check_every=10, p_star=pstar,
-                                     tol=1e-6, history=False)[0]
-        for _ in range(args.warmup):
-            run()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(torch.cuda.current_stream())
-        for _ in range(args.steps):
-            res = run()
-        e1.record(torch.cuda.current_stream())
-        e1.synchronize()
-        arms[f"T={T}"] = {"ccp_iters": int(res["iters"]), "total_iters": int(res["iters"]) + T,
-                          "converged": bool(res["converged"]), "rel_gap": res["rel_gap"],
-                          "op_norm": res["op_norm"], "ms": e0.elapsed_time(e1) / args.steps}
+    with ClockSampler(local) as clk:
+        for T in (0, 10, 30, 100, 300):
+            def run():
+                ub, vb = equilibrate(op, T, f32)
+                x = torch.zeros(n, **f32)
+                return sme.sme_ccp_lasso(op, ub, vb, b32, x, lam=lam, max_iters=20000, check_every=10, p_star=pstar,
+                                         tol=1e-6, history=False)[0]
+            for _ in range(args.warmup):
+                run()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(torch.cuda.current_stream())
+            for _ in range(args.steps):
+                res = run()
+            e1.record(torch.cuda.current_stream())
+            e1.synchronize()
+            arms[f"T={T}"] = {"ccp_iters": int(res["iters"]), "total_iters": int(res["iters"]) + T,
+                              "converged": bool(res["converged"]), "rel_gap": res["rel_gap"],
+                              "op_norm": res["op_norm"], "ms": e0.elapsed_time(e1) / args.steps}
     best = min((a["total_iters"] for k, a in arms.items() if k != "T=0" and a["converged"]), default=None)
     line = {
         "metric": "CCP (Section 5.2) iterations and wall-time to a relative Lasso gap of 1e-6, with and without "
@@ -920,19 +935,24 @@ def run_ccp(args, rank, world, local):
                                f"Algorithm 1 with k=1, gamma=0.1",
                    "m": m, "n": n, "nnz": A.nnz, "lambda": lam,
                    "l2": "small problem (L2-resident): latency-bound, not a bandwidth figure"},
-        "p_star": pstar, "p_star_drift_last_5000_iters": drift, "arms": arms,
+        "p_star": pstar, "p_star_drift_last_5000_iters": drift, "arms": arms, "clocks": clk.summary(),
         "speedup_iters_T100": (arms["T=0"]["total_iters"] / arms["T=100"]["total_iters"]
                                if arms["T=0"]["converged"] and arms["T=100"]["converged"] else None),
         "best_total_iters_with_equilibration": best,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     sme.sme_op_destroy(op)
     sme.sme_op_destroy(op64)
-    return 0
+    return line
 
 
 def run_lsqr_paper(args, rank, world, local):
+    line = lsqr_paper_line(args, rank, world, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def lsqr_paper_line(args, rank, world, local):
     """Section 5.1's experiment: square A as in Section 4 (n = 1e4, 1% uniform-random nonzeros, N(0,1) values,
     factors e^{N(1,1)}), b = A x*, LSQR (FP32 vectors, FP64 scalars and residual checks) from x = 0 without
     equilibration and after T = 10, 30, 100, 300 iterations of Algorithm 1 (one probe pair, the paper's
@@ -955,35 +975,36 @@ def run_lsqr_paper(args, rank, world, local):
     ops = {1e-4: (sme.sme_op_create_csr(n, n, A.row_ptr, A.col_idx, A.vals), torch.float32),
            1e-6: (sme.sme_op_create_csr(n, n, A.row_ptr, A.col_idx, A.vals.astype(np.float64)), torch.float64)}
     arms = {}
-    for T in (0, 10, 30, 100, 300):
-        res = {}
-        for tol in (1e-4, 1e-6):
-            op, td = ops[tol]
-            kw = dict(dtype=td, device="cuda")
-            bt = torch.tensor(b, **kw)
+    with ClockSampler(local) as clk:
+        for T in (0, 10, 30, 100, 300):
+            res = {}
+            for tol in (1e-4, 1e-6):
+                op, td = ops[tol]
+                kw = dict(dtype=td, device="cuda")
+                bt = torch.tensor(b, **kw)
 
-            def run():
-                ub = vb = None
-                if T > 0:
-                    z = [torch.zeros(n, **kw) for _ in range(4)]
-                    sme.sme_equilibrate(op, *z, T=T, k=1, seed=0)
-                    ub, vb = z[2], z[3]
-                x = torch.zeros(n, **kw)
-                return sme.sme_lsqr(op, ub, vb, bt, x, tol=tol, max_iters=20000, check_every=10)
-            for _ in range(args.warmup):
-                run()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record(torch.cuda.current_stream())
-            for _ in range(args.steps):
-                r = run()
-            e1.record(torch.cuda.current_stream())
-            e1.synchronize()
-            res[f"{tol:g}"] = {"lsqr_iters": int(r["iters"]), "total_iters": int(r["iters"]) + T,
-                               "converged": bool(r["converged"]), "rel_residual": r["rel_residual"],
-                               "vectors": "f32" if td == torch.float32 else "f64",
-                               "ms": e0.elapsed_time(e1) / args.steps}
-        arms[f"T={T}"] = res
+                def run():
+                    ub = vb = None
+                    if T > 0:
+                        z = [torch.zeros(n, **kw) for _ in range(4)]
+                        sme.sme_equilibrate(op, *z, T=T, k=1, seed=0)
+                        ub, vb = z[2], z[3]
+                    x = torch.zeros(n, **kw)
+                    return sme.sme_lsqr(op, ub, vb, bt, x, tol=tol, max_iters=20000, check_every=10)
+                for _ in range(args.warmup):
+                    run()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(torch.cuda.current_stream())
+                for _ in range(args.steps):
+                    r = run()
+                e1.record(torch.cuda.current_stream())
+                e1.synchronize()
+                res[f"{tol:g}"] = {"lsqr_iters": int(r["iters"]), "total_iters": int(r["iters"]) + T,
+                                   "converged": bool(r["converged"]), "rel_residual": r["rel_residual"],
+                                   "vectors": "f32" if td == torch.float32 else "f64",
+                                   "ms": e0.elapsed_time(e1) / args.steps}
+            arms[f"T={T}"] = res
     best4 = min(a["0.0001"]["total_iters"] for k, a in arms.items() if k != "T=0" and a["0.0001"]["converged"])
     line = {
         "metric": "LSQR (Section 5.1) iterations and wall-time to relative residuals 1e-4 and 1e-6, with and "
@@ -995,23 +1016,24 @@ def run_lsqr_paper(args, rank, world, local):
                                f"row/column factors e^N(1,1); b = A x*, x* ~ N(0,1); Algorithm 1 with k=1, "
                                f"gamma=0.1; iteration cap 20000; FP64 scalars and residual checks throughout",
                    "n": n, "nnz": A.nnz, "l2": "small problem (L2-resident): latency-bound"},
-        "arms": arms,
+        "arms": arms, "clocks": clk.summary(),
         "iteration_ratio_1e-4_plain_over_best": (arms["T=0"]["0.0001"]["total_iters"] / best4
                                                  if arms["T=0"]["0.0001"]["converged"] else None),
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     for op, _ in ops.values():
         sme.sme_op_destroy(op)
-    return 0
+    return line
 
 
 def secondary_lines(args, rank, world, local, batched_mats):
-    """The dense (BF16 and FP8-E4M3) and batched workloads at their full sizes, each with its own timed region,
-    roofline and clock record (5 timed steps after 3 warm-up steps; the batched per-matrix LSQR is left to
-    --workload batched)."""
+    """The other workloads at their full sizes, each with its own timed region and clock record: dense (BF16 and
+    FP8-E4M3) and batched with their rooflines (5 timed steps after 3 warm-up steps; the batched per-matrix LSQR
+    is left to --workload batched), then the learned warm start, CCP (Section 5.2) and LSQR (Section 5.1), one
+    timed solve per arm after one untimed.  A workload that fails records its error here instead of ending the
+    line."""
     import copy
     import gc
+    import traceback
 
     sub = copy.copy(args)
     sub.steps, sub.warmup, sub.T = min(args.steps, 5), max(3, min(args.warmup, 3)), 500
@@ -1025,6 +1047,19 @@ def secondary_lines(args, rank, world, local, batched_mats):
     sub_b.no_lsqr = True
     bl = batched_line(sub_b, rank, world, local, mats=batched_mats)
     out["batched"] = {key: bl[key] for key in keep if key in bl}
+    del bl
+    gc.collect()
+    sub_s = copy.copy(args)
+    sub_s.steps, sub_s.warmup, sub_s.T = 1, 1, 500
+    for name, fn in (("learned", learned_line), ("ccp", ccp_line), ("lsqr", lsqr_paper_line)):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn(sub_s, rank, world, local)
+        except Exception as e:  # recorded on the line; the default workload's result stands
+            out[name] = {"error": f"{type(e).__name__}: {e}", "trace": traceback.format_exc()[-800:]}
+        if out[name] is not None:
+            out[name]["wall_s"] = time.perf_counter() - t0
+        gc.collect()
     return out
 
 
