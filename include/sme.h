@@ -408,7 +408,10 @@ sme_status sme_ccp_lasso(sme_op op, const void *u_bar, const void *v_bar, const 
  *
  * Network: 8 normalised features -> 128 (ReLU) -> 128 (ReLU) -> 1, BF16 weights for the forward pass,
  * FP32 master weights and FP32 accumulation, trained on the device by sme_mlp_train_step (mean squared
- * error, Adam).  Features of row i (column j), see sme_op_features:
+ * error, Adam).  The 128 x 128 layer and its gradients run on the tensor cores (BF16 operands, the
+ * activations split into several BF16 terms so that the results keep FP32 accuracy).  Their completion
+ * waits are bounded: one that runs out leaves NaN in that call's outputs and sets a status word that the
+ * next sme_mlp_gradient / sme_mlp_train_step with a loss read reports as SME_ERR_TIMEOUT.  Features of row i (column j), see sme_op_features:
  *   [ 1/2 log of the k = 8 sketch of the squared norm (sme_estimate at u = v = 0, t = 1),
  *     log(1 + nonzeros), log(mean |A_ij|), side (0 rows, 1 columns),
  *     mean sketch log-norm of the rows, of the columns, log m, log n ].
