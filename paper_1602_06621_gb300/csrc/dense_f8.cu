@@ -2,7 +2,7 @@
 //
 // The matrix stays E4M3 in HBM (one byte per entry, with one FP32 scale c_i per row: A_ij = c_i q_ij),
 // as A and a transposed copy A^T, both K-blocked in 128 x 128-byte blocks so that every TMA tile load is
-// one contiguous 16 KB run.  The B operand of each product is a single E4M3 term (survey reading of the
+// one contiguous 16 KB run.  The B operand of each product is a single E4M3 term (the single-term reading of the
 // Section 3.1 estimator on dense A: the +-1 probes are exact, the scaling e^{x_j} is rounded to the 4
 // significant bits of E4M3, a relative error of at most 2^-4 per scaling):
 //     B[p][j] = e4m3( 2^S e^{x_j} c_j ) * s_jp          (c_j = 1 on the forward side)
