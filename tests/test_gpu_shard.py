@@ -168,3 +168,28 @@ def test_split_part_refuses_steps_without_a_matching_begin():
         torch.cuda.synchronize()
     finally:
         sme.sme_op_destroy(op)
+
+
+@pytest.mark.parametrize("P", [2, 4])
+def test_split_full_size_equals_unsplit(P):
+    """The 1e6 x 5e5 workload the split bench runs (20 nonzeros per row, FP32, k = 32): P parts on one GPU
+    (device-copy exchange), T = 3 from zero, bit for bit against the unsplit operator."""
+    import torch
+    A = I.workload_large(1.0, seed=2)
+    k, T = 32, 3
+    op = sme.sme_op_create_csr(A.m, A.n, A.row_ptr, A.col_idx, A.vals)
+    try:
+        z = [torch.zeros(x, device="cuda") for x in (A.m, A.n, A.m, A.n)]
+        sme.sme_equilibrate(op, *z, T=T, k=k, seed=0)
+        ref = [x.cpu().numpy() for x in z]
+        del z
+    finally:
+        sme.sme_op_destroy(op)
+    parts = _parts(A, P, k, torch.float32)
+    try:
+        SH.run(parts, SH.LocalExchange(), T=T, k=k, seed=0)
+        got = _gather(parts, A)
+    finally:
+        _destroy(parts)
+    for g, r in zip(got, ref):
+        np.testing.assert_array_equal(g, r.astype(np.float64))
