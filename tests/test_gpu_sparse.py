@@ -227,6 +227,44 @@ def test_ragged_and_degenerate_shapes_fp64(case, k):
     assert np.all(np.abs(zv - O.col_estimate(A, u, v, O.probe_signs(9, 2, 1, A.m, k))) <= 1e-12 * c2 + 1e-300)
 
 
+@pytest.mark.parametrize("case", range(5))
+@pytest.mark.parametrize("k", [16, 32])
+def test_ragged_and_degenerate_shapes_fp32(case, k):
+    """The FP32 kernels (the bench's path) on the same shapes: every one of 20 steps against the oracle's step
+    from the GPU's state (norm-wise 1e-4, the method's FP32 target), and one estimate at random u, v within a
+    derived FP32 rounding bound: a row of L nonzeros with c_j = |a_ij| e^{v_j} carries at most
+    (6 L + 80) 2^-24 e^{2 u_i} (sum_j c_j)^2 (the kernel's two FP32 sums per probe, their difference, the
+    products, the FP32 table value e^{v_j}, the squares and their mean)."""
+    A = _ragged_cases()[case]
+    A = I.CSR(A.m, A.n, A.row_ptr, A.col_idx, A.vals.astype(np.float32))
+    op, dt = make_op(A, sme.SME_F32)
+    try:
+        worst, _ = trajectory_parity(op, dt, A, T=20, k=k, seed=9)
+        rng = np.random.default_rng(case)
+        u, v = rng.normal(0, 0.5, A.m).astype(np.float32), rng.normal(0, 0.5, A.n).astype(np.float32)
+        zu, zv = gpu_estimate(op, dt, u, v, t=2, k=k, seed=9)
+    finally:
+        sme.sme_op_destroy(op)
+    assert worst <= 1e-4, worst
+    u64, v64 = u.astype(np.float64), v.astype(np.float64)
+    S = O.OracleCSR.from_any(A)
+    for z, own, other, signs, rp, ci, vals in (
+            (zu, u64, v64, O.probe_signs(9, 2, 0, A.n, k), A.row_ptr, A.col_idx, A.vals),
+            (zv, v64, u64, O.probe_signs(9, 2, 1, A.m, k), *_csc(A))):
+        ref = O.row_estimate(S, u64, v64, signs) if z is zu else O.col_estimate(S, u64, v64, signs)
+        L = np.diff(rp).astype(np.float64)
+        s1 = np.array([np.sum(np.abs(vals[rp[i]:rp[i + 1]].astype(np.float64)) * np.exp(other[ci[rp[i]:rp[i + 1]]]))
+                       for i in range(len(rp) - 1)])
+        bound = (6 * L + 80) * 2.0 ** -24 * np.exp(2 * own) * s1 ** 2
+        assert np.all(np.abs(z - ref) <= bound + 1e-30)
+
+
+def _csc(A):
+    import scipy.sparse as sps
+    C = sps.csr_matrix((A.vals, A.col_idx, A.row_ptr), shape=(A.m, A.n)).tocsc()
+    return C.indptr, C.indices, C.data
+
+
 @pytest.mark.parametrize("dtype_code", [sme.SME_F64, sme.SME_F32])
 def test_resume_and_rerun_are_bitwise_identical(small, dtype_code):
     A = small[0]
