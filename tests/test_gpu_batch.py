@@ -66,6 +66,31 @@ def test_batch_fp64_matches_oracle_per_matrix():
         assert rel_norm(mine, ref) <= 1e-10
 
 
+def test_batch_of_degenerate_matrices_matches_oracle_per_matrix():
+    """A batch holding a matrix with empty rows and columns, a single row, a single column, a 1 x 1 matrix and
+    a matrix with no nonzeros at all, between ordinary ones (FP64, T = 6, k = 16): each matrix against the
+    oracle run on it alone with its own probe streams."""
+    import torch
+    mats = [I.sparse_uniform_density(37, 23, 0.08, seed=5, dtype=np.float64),
+            I.sparse_uniform_density(1, 5, 0.8, seed=6, dtype=np.float64),
+            I.sparse_uniform_density(300, 200, 0.05, seed=9, dtype=np.float64),
+            I.sparse_uniform_density(5, 1, 0.8, seed=7, dtype=np.float64),
+            I.CSR(1, 1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([2.5])),
+            I.CSR(40, 33, np.zeros(41, np.int32), np.zeros(0, np.int32), np.zeros(0)),
+            I.sparse_uniform_density(64, 90, 0.1, seed=10, dtype=np.float64)]
+    b = sme.sme_batch_create(mats)
+    try:
+        count, ro, co = sme.sme_batch_get_info(b)
+        assert count == len(mats)
+        got = _batch_run(b, mats, torch.float64, T=6, k=16, seed=3)
+    finally:
+        sme.sme_batch_destroy(b)
+    for i, A in enumerate(mats):
+        ref = O.equilibrate(A, T=6, k=16, seed=3, stream_base=2 * i)
+        mine = (got[0][ro[i]:ro[i + 1]], got[1][co[i]:co[i + 1]], got[2][ro[i]:ro[i + 1]], got[3][co[i]:co[i + 1]])
+        assert rel_norm(mine, ref) <= 1e-10, i
+
+
 def test_batch_with_long_rows_every_step_fp64():
     """Matrices of 150-300 nonzeros per row in one batch: the batch's slices are shared among warps (split
     accumulation) while each matrix keeps its own targets and probe streams.  Every step of every matrix
