@@ -48,11 +48,13 @@ def _gpu_estimate(op, m, n, u, v, t, k, seed):
     return zu.cpu().double().numpy(), zv.cpu().double().numpy()
 
 
-@pytest.mark.parametrize("m,n", [(256, 256), (384, 256), (256, 512), (1280, 384), (384, 2560)])
+@pytest.mark.parametrize("m,n", [(128, 128), (128, 1152), (256, 256), (384, 256), (256, 512), (1280, 384),
+                                 (384, 2560)])
 @pytest.mark.parametrize("k", [128, 256])
 def test_dense_estimate_matches_oracle(m, n, k):
-    """Shapes with an odd number of 128-row tiles (384, 1280) exercise the spare CTA of the last cluster;
-    384 x 2560 runs more clusters than one per product."""
+    """Shapes with an odd number of 128-row tiles (128, 384, 1280) exercise the spare CTA of the last cluster
+    (at 128 one tile per side, a single cluster per product); 384 x 2560 runs more clusters than one per
+    product."""
     Ad, Af = _bf16_matrix(m, n, seed=m + n + k)
     op = sme.sme_op_create_dense(m, n, Ad, dtype=sme.SME_BF16)
     try:
@@ -163,7 +165,7 @@ def _rounded_signs(seed, t, stream, x, c, k):
     return O.probe_signs(seed, t, stream, len(x), k) * ratio[:, None]
 
 
-@pytest.mark.parametrize("m,n", [(256, 256), (384, 256), (1280, 384), (384, 2560)])
+@pytest.mark.parametrize("m,n", [(128, 128), (1152, 128), (256, 256), (384, 256), (1280, 384), (384, 2560)])
 @pytest.mark.parametrize("k", [128, 256])
 def test_dense_fp8_representable_scalings_match_oracle(m, n, k):
     """Scalings chosen so that e^{v_j} and e^{u_i} c_i are E4M3 values: the operands are exact, so the E4M3
