@@ -68,3 +68,41 @@ def test_degenerate_shapes_are_rejected():
     lib = sme.load()
     p = sme.sme_equil_params(0, 0, 0, 0, 10, 32, 1, 0, 0, 0, 0)
     assert lib.sme_equilibrate(None, ctypes.byref(p), None, None, None, None, None) == -1
+
+
+def _prototypes():
+    """Parameter lists of every function include/sme.h declares, comments removed: name -> [parameter text]."""
+    out = {}
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for name, params in re.findall(r"\b(sme_\w+)\s*\(([^()]*)\)\s*;", text):
+            params = params.strip()
+            out[name] = [] if params in ("", "void") else [p.strip() for p in params.split(",")]
+    return out
+
+
+def test_binding_argument_lists_match_the_header():
+    """The ctypes binding declares as many arguments as the header, pointers where the header has pointers
+    and 64-bit integers where it has 64-bit integers, so a drifting signature fails here rather than
+    corrupting a call."""
+    protos = _prototypes()
+    assert len(protos) == len(_declared())
+    for name, params in protos.items():
+        argtypes, _ = sme.SIGNATURES[name]
+        assert len(argtypes) == len(params), (name, params)
+        for p, a in zip(params, argtypes):
+            is_ptr = "*" in p or p.split()[0] in ("sme_op", "sme_batch", "sme_mlp")
+            if is_ptr:
+                assert a is ctypes.c_void_p or issubclass(a, ctypes._Pointer) or a is ctypes.c_char_p, (name, p)
+            elif p.split()[0] in ("int64_t",):
+                assert a is ctypes.c_int64, (name, p)
+            elif p.split()[0] in ("uint64_t",):
+                assert a is ctypes.c_uint64, (name, p)
+            elif p.split()[0] in ("double",):
+                assert a is ctypes.c_double, (name, p)
+            elif p.split()[0] in ("float",):
+                assert a is ctypes.c_float, (name, p)
