@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(TT, 1)
             x[f] = valid ? (X[(base + tid) * MLP_IN + f] - norm[f]) * norm[MLP_IN + f] : 0.f;
         // Layer 1 into the A operand of the forward product; its ReLU mask kept for dZ1.
         uint32_t mask1[MLP_H / 32];
-#pragma unroll
+#pragma unroll 1
         for (int c = 0; c < MLP_H / 32; ++c) {
             uint32_t m = 0;
 #pragma unroll
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(TT, 1)
         // Layer 2's ReLU and layer 3 (FP32) from row tid of Z.
         float yv = 0.f;
         uint32_t mask2[MLP_H / 32];
-#pragma unroll
+#pragma unroll 1
         for (int c = 0; c < MLP_H / 32; ++c) {
             float z[32];
             tmem_ld32(t_lane + c * 32, z);
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(TT, 1)
         gb3 += dy;
         // dW3 partials and D2 = dy w3 (h2 > 0), written over the forward operand (its product is complete) as
         // the A operand of dH1.
-#pragma unroll
+#pragma unroll 1
         for (int c = 0; c < MLP_H / 32; ++c) {
             float z[32];
             tmem_ld32(t_lane + c * 32, z);
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(TT, 1)
         for (int c = 0; c < TT / CH; ++c) {
             if (tid / CH == c) {  // whole warps
                 const int sl = tid - c * CH;
-#pragma unroll
+#pragma unroll 1
                 for (int cc = 0; cc < MLP_H / 32; ++cc) {
                     float g[32];
                     tmem_ld32(t_lane + cc * 32, g);
